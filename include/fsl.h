@@ -1,0 +1,175 @@
+/*
+ * fsl.h -- C ABI of libfsl, a GB300 (sm_103a) free-surface lattice Boltzmann
+ * (FSLBM) time step with the five refilling schemes compared in Schwarzmeier &
+ * Ruede, "Comparison of refilling schemes in the free-surface lattice
+ * Boltzmann method" (arXiv 2207.14496).
+ *
+ * One handle advances one domain.  Every step runs entirely in the library's
+ * CUDA kernels on the stream bound at creation:
+ *   1. pull stream + collide (SRT Eq. nm-lbm-collision-operator, or TRT) with
+ *      Guo forcing (Eq. nm-lbm-force-guo), halfway bounce-back at walls, the
+ *      free-surface anti-bounce-back condition (Eq. nm-fslbm-boundary-condition)
+ *      for PDFs arriving from gas, and the interface mass flux
+ *      (Eq. nm-fslbm-mass-flux, Sec. 2.2, with Thuerey's treatment of
+ *      unnecessary interface cells);
+ *   2. cell conversion with the threshold epsilon_phi (Sec. 2.2) over
+ *      warp-ballot-compacted candidate lists;
+ *   3. refilling of gas->interface cells (Sec. 3.1: EQ, EQ+NEQ, GEQ, EXT, AVG);
+ *   4. excess-mass redistribution (Eq. nm-fslbm-excess-mass);
+ *   5. Parker-Youngs normals and curvature kappa = -div(n_hat) (Sec. 2.2) for
+ *      the Laplace pressure (Eqs. nm-fslbm-pressure-gas, nm-fslbm-pressure-laplace).
+ *
+ * Conventions for every entry point
+ *   - Status: 0 on success, a negative fsl_status on failure.  No entry point
+ *     aborts or traps; device-side conditions (instability) are latched in a
+ *     device status word and reported by fsl_observe(FSL_OBS_STATUS).
+ *   - Memory: the caller owns the device workspace (one allocation of
+ *     fsl_workspace_bytes bytes, 256-byte aligned) and the CUDA stream.  The
+ *     library never calls cudaMalloc/cudaFree; it mallocs only the small host
+ *     handle and temporary host buffers inside fsl_observe.
+ *   - Synchronisation: fsl_step is asynchronous on the bound stream.
+ *     fsl_init_fill, fsl_observe, fsl_save and fsl_load synchronise the stream
+ *     before returning, so host buffers may be reused immediately.
+ *   - Threading: a handle is bound to one stream and is not thread-safe.
+ *   - Layout of host arrays: cell (i, j, k) at index i + nx (j + ny k), x
+ *     fastest; PDF arrays are q planes of nx*ny*nz values, direction order
+ *     rest, 6 faces, 12 edges (, 8 corners) as listed in fsl_lattice_table.
+ */
+#ifndef FSL_H
+#define FSL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fsl_handle fsl_handle;
+
+typedef enum {
+  FSL_OK = 0,
+  FSL_ERR_ARG = -1,       /* invalid argument or configuration */
+  FSL_ERR_CUDA = -2,      /* a CUDA runtime call failed (message: fsl_last_error) */
+  FSL_ERR_WORKSPACE = -3, /* workspace missing, misaligned or too small */
+  FSL_ERR_UNSTABLE = -4,  /* |u| >= c_s or a NaN appeared; steps are frozen */
+  FSL_ERR_TIMEOUT = -5,   /* a bounded device wait gave up */
+  FSL_ERR_STATE = -6      /* call out of order (e.g. step before init_fill) */
+} fsl_status;
+
+enum { FSL_D3Q19 = 19, FSL_D3Q27 = 27 };
+enum { FSL_SRT = 0, FSL_TRT = 1 };
+/* PDF storage / collision precision.  FP64: FP64 storage and arithmetic,
+ * bit-reproducible against a plain FP64 evaluation in the documented
+ * operation order.  FP32: FP32 storage and arithmetic.  MIXED_FP16 /
+ * MIXED_BF16: PDFs stored as 16-bit offsets f_i - w_i (FP16 scaled by 2^15),
+ * collision and mass flux in FP32; cell mass, excess mass and reductions stay
+ * FP64 in every mode. */
+enum { FSL_FP64 = 0, FSL_FP32 = 1, FSL_MIXED_FP16 = 2, FSL_MIXED_BF16 = 3 };
+/* Refilling schemes of Sec. 3.1. */
+enum { FSL_REFILL_EQ = 0, FSL_REFILL_EQ_NEQ = 1, FSL_REFILL_GEQ = 2, FSL_REFILL_EXT = 3,
+       FSL_REFILL_AVG = 4 };
+/* Reading switches (fsl_config.options). */
+enum {
+  FSL_OPT_SIMPLE_FLUX = 1u,      /* plain Eq. nm-fslbm-mass-flux, no Thuerey table */
+  FSL_OPT_GEQ_LITERAL_NU = 2u,   /* GEQ prefactor 1/(2 c_s^2 nu) as printed (default 1/(2 c_s^2 omega)) */
+  FSL_OPT_NEQ_LITERAL_MEAN = 4u, /* EQ+NEQ: f_i(y) - f_i^eq(rho_bar, u_bar) as printed */
+  FSL_OPT_LAPLACE_LITERAL = 8u   /* p_G = p_V - 2 sigma kappa (default p_G = p_V + sigma K) */
+};
+
+typedef struct {
+  int lattice;      /* FSL_D3Q19 | FSL_D3Q27 */
+  int collision;    /* FSL_SRT | FSL_TRT */
+  double trt_magic; /* TRT magic parameter Lambda (3/16 typical) */
+  int precision;    /* FSL_FP64 | FSL_FP32 | FSL_MIXED_FP16 | FSL_MIXED_BF16 */
+  int refill;       /* FSL_REFILL_* */
+  int nx, ny, nz;   /* cells; each >= 1 */
+  int periodic[3];  /* per axis: 1 periodic, 0 no-slip (bounce-back) walls on both faces */
+  double nu;        /* kinematic viscosity, lattice units; tau = 3 nu + 1/2 */
+  double gravity[3];/* body acceleration g; force F = rho g (Guo) */
+  double sigma;     /* surface tension (0: no Laplace pressure) */
+  double p_volume;  /* volume (atmospheric) gas pressure, 1/3 for rho = 1 */
+  double eps_phi;   /* conversion threshold epsilon_phi (1e-2 in the paper) */
+  unsigned options; /* FSL_OPT_* */
+} fsl_config;
+
+/* Workspace size for a configuration.  bytes: out.  FSL_ERR_ARG for an
+ * invalid configuration. */
+fsl_status fsl_workspace_bytes(const fsl_config* cfg, size_t* bytes);
+
+/* Bind a configuration to a caller-owned device workspace and CUDA stream
+ * (cudaStream_t passed as void*; NULL = legacy default stream).
+ * d_workspace: device pointer, 256-byte aligned, >= fsl_workspace_bytes.
+ * out: receives the host handle (release with fsl_destroy). */
+fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
+                      fsl_handle** out);
+
+/* Initial state (Sec. 2.2 cell types): phi (host, N doubles) gives the fill
+ * level; phi >= 1 liquid, phi <= 0 gas, else interface; a liquid cell touching
+ * gas becomes interface (closed layer).  u0 (host, 3N doubles, xyz per cell)
+ * or NULL for rest.  obstacle (host, N bytes, nonzero = solid) or NULL.
+ * h_ref: height along the gravity axis where rho = 1; the initial density is
+ * rho = 1 + 3 g_a (x_a + 1/2 - h_ref) (hydrostatic); NaN disables it.
+ * PDFs start at f^eq(rho, u0), m = phi rho.  Synchronises the stream. */
+fsl_status fsl_init_fill(fsl_handle* h, const double* phi, const double* u0,
+                         const unsigned char* obstacle, double h_ref);
+
+/* Advance nsteps time steps (asynchronous).  After an instability has been
+ * latched, further steps do nothing.  Launch sequence is captured once into a
+ * CUDA graph per distinct nsteps and replayed. */
+fsl_status fsl_step(fsl_handle* h, int nsteps);
+
+/* Observables (fsl_observe `what`).  host_out must hold `bytes` bytes. */
+enum {
+  FSL_OBS_TOTAL_MASS = 1,    /* double: sum of liquid zeroth moments + interface m + lost mass */
+  FSL_OBS_COLUMN_HEIGHT = 2, /* double: sum_j phi(0, j, k), averaged over k (surface elevation + depth) */
+  FSL_OBS_FRONT = 3,         /* double: 1 + largest i of an interface cell with j = 0 */
+  FSL_OBS_HEIGHT = 4,        /* double: 1 + largest j of an interface cell with i = 0 */
+  FSL_OBS_MAX_VELOCITY = 5,  /* double: max |u| over fluid cells */
+  FSL_OBS_STATUS = 6,        /* int64[2]: {FSL_OK or FSL_ERR_UNSTABLE, first unstable step or -1} */
+  FSL_OBS_STEP = 7,          /* int64: steps taken */
+  FSL_OBS_COUNTS = 8,        /* int64[4]: last step's {filled, emptied, new interface, interface} */
+  FSL_OBS_LOST_MASS = 9,     /* double: mass of converted cells that had no interface neighbour */
+  FSL_OBS_TRACE = 10,        /* double[3 * steps]: per step {column height at i=0, front, height} */
+  FSL_OBS_FIELD_PDF = 16,    /* double[q N]: stored post-collision PDFs (valid in fluid cells) */
+  FSL_OBS_FIELD_TYPES = 17,  /* uint8[N]: 0 gas, 1 interface, 2 liquid, 3 obstacle */
+  FSL_OBS_FIELD_PHI = 18,    /* double[N]: fill level */
+  FSL_OBS_FIELD_MASS = 19,   /* double[N]: cell mass m (meaningful in interface cells) */
+  FSL_OBS_FIELD_KAPPA = 20   /* double[N]: curvature K = -div(n_hat) (interface cells, sigma != 0) */
+};
+/* Reads an observable into host memory; synchronises the stream.
+ * FSL_ERR_ARG if `bytes` is smaller than the observable. FSL_OBS_TRACE holds
+ * at most fsl_trace_capacity steps (oldest first; extra steps overwrite the
+ * ring) and writes min(steps, capacity) records. */
+fsl_status fsl_observe(fsl_handle* h, int what, void* host_out, size_t bytes);
+
+/* Enable (every >= 1) or disable (0) the per-step trace of
+ * FSL_OBS_TRACE; clears the ring.  Capacity in steps: fsl_trace_capacity. */
+fsl_status fsl_set_trace(fsl_handle* h, int every);
+int fsl_trace_capacity(void);
+
+/* Checkpoint: fsl_state_bytes gives the size; fsl_save copies the full
+ * simulation state to host memory, fsl_load restores it (same config).
+ * Resuming from a checkpoint is bit-identical to an uninterrupted run. */
+fsl_status fsl_state_bytes(const fsl_handle* h, size_t* bytes);
+fsl_status fsl_save(fsl_handle* h, void* host_dst, size_t bytes);
+fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes);
+
+/* Release the handle (the workspace and stream stay with the caller). */
+fsl_status fsl_destroy(fsl_handle* h);
+
+/* Lattice table used by the library: c (3q ints) and w (q doubles).
+ * FSL_ERR_ARG for an unknown lattice. */
+fsl_status fsl_lattice_table(int lattice, int* c3q, double* w);
+
+/* Number of kernel launches one fsl_step(1) issues. */
+int fsl_launches_per_step(const fsl_handle* h);
+
+/* Static description of a status code; last CUDA error text of this thread. */
+const char* fsl_status_string(fsl_status s);
+const char* fsl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FSL_H */

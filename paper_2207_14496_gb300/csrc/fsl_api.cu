@@ -1,0 +1,560 @@
+// Host side of the C ABI declared in include/fsl.h: configuration checks,
+// workspace carving, initial state, step launches (captured into CUDA graphs),
+// observation, checkpointing.  No device memory is allocated here; every
+// device buffer is carved out of the caller's workspace.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "fsl.h"
+#include "fsl_kernels.cuh"
+
+using namespace fsl;
+
+namespace {
+
+thread_local std::string g_err;
+
+fsl_status cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return FSL_ERR_CUDA;
+}
+#define FSL_CK(call)                                   \
+  do {                                                 \
+    cudaError_t e_ = (call);                           \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+enum Region {
+  R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST,
+  R_LIF, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_CTRL, R_TRACE, R_RED, R_COUNT
+};
+
+bool valid_config(const fsl_config* c) {
+  if (!c) return false;
+  if (c->lattice != FSL_D3Q19 && c->lattice != FSL_D3Q27) return false;
+  if (c->collision != FSL_SRT && c->collision != FSL_TRT) return false;
+  if (c->precision < FSL_FP64 || c->precision > FSL_MIXED_BF16) return false;
+  if (c->refill < FSL_REFILL_EQ || c->refill > FSL_REFILL_AVG) return false;
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return false;
+  if (!(c->nu > 0.0) || !std::isfinite(c->nu)) return false;
+  if (c->collision == FSL_TRT && !(c->trt_magic > 0.0)) return false;
+  if (!(c->eps_phi >= 0.0)) return false;
+  for (int a = 0; a < 3; ++a)
+    if (!std::isfinite(c->gravity[a])) return false;
+  if (!std::isfinite(c->sigma) || !std::isfinite(c->p_volume)) return false;
+  const long long sx = ((long long)c->nx + 31) / 32 * 32;
+  const long long cells = sx * c->ny * (long long)c->nz;
+  const long long plane = (cells + 127) / 128 * 128;
+  if (plane * (long long)c->lattice >= (1ll << 31) * 8ll) return false;
+  if (cells >= (1ll << 31) - 1) return false;
+  return true;
+}
+
+void make_geom(const fsl_config* c, Geom* g) {
+  g->nx = c->nx;
+  g->ny = c->ny;
+  g->nz = c->nz;
+  g->sx = (c->nx + 31) / 32 * 32;
+  g->cells = (long long)g->sx * c->ny * c->nz;
+  g->plane = (g->cells + 127) / 128 * 128;
+  for (int a = 0; a < 3; ++a) g->periodic[a] = c->periodic[a] ? 1 : 0;
+}
+
+void make_phys(const fsl_config* c, Phys* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->q = c->lattice;
+  p->trt = c->collision == FSL_TRT;
+  p->refill = c->refill;
+  p->options = c->options;
+  // Eq. nm-lbm-viscosity: nu = c_s^2 (tau - 1/2)
+  p->tau = 3.0 * c->nu + 0.5;
+  p->omega = 1.0 / p->tau;
+  p->lam_e = p->omega;
+  // TRT magic parameter Lambda = (1/lam_e - 1/2)(1/lam_o - 1/2)
+  p->lam_o = 1.0 / (0.5 + c->trt_magic / (1.0 / p->lam_e - 0.5));
+  p->pre_e = 1.0 - 0.5 * p->lam_e;
+  p->pre_o = 1.0 - 0.5 * p->lam_o;
+  p->gaxis = -1;
+  for (int a = 0; a < 3; ++a) {
+    p->g[a] = c->gravity[a];
+    if (c->gravity[a] != 0.0) p->gaxis = a;
+  }
+  p->sigma = c->sigma;
+  p->p_v = c->p_volume;
+  p->eps = c->eps_phi;
+  // GEQ prefactor: 1/(2 c_s^2 omega) = 1.5 tau, or the printed 1/(2 c_s^2 nu)
+  p->geq_coef = (c->options & FSL_OPT_GEQ_LITERAL_NU) ? 1.5 / c->nu : 1.5 * p->tau;
+  p->thr_hi = 1.0 + c->eps_phi;
+  p->thr_lo = 0.0 - c->eps_phi;
+}
+
+void region_sizes(const fsl_config* c, const Geom& g, size_t* sz) {
+  const size_t sb = storage_bytes(c->precision);
+  const size_t cells = (size_t)g.cells;
+  sz[R_PDF0] = sz[R_PDF1] = (size_t)g.plane * c->lattice * sb;
+  sz[R_FLAGS] = sz[R_CLAIM] = cells;
+  sz[R_PHI] = sz[R_PHINEW] = sz[R_MASS] = sz[R_RHO] = sz[R_KAPPA] = sz[R_MEX] = sz[R_LOST] =
+      cells * sizeof(double);
+  for (int r = R_LIF; r <= R_LRECV; ++r) sz[r] = cells * sizeof(int);
+  sz[R_CTRL] = sizeof(Ctrl);
+  sz[R_TRACE] = (size_t)kTraceCapacity * 3 * sizeof(double);
+  sz[R_RED] = (size_t)(2 * kReduceBlocks + 16) * sizeof(double);
+}
+
+size_t layout(const fsl_config* c, const Geom& g, size_t* off) {
+  size_t sz[R_COUNT];
+  region_sizes(c, g, sz);
+  size_t at = 0;
+  for (int r = 0; r < R_COUNT; ++r) {
+    off[r] = at;
+    at = align256(at + sz[r]);
+  }
+  return at;
+}
+
+const Launch* pick(int precision, int q) {
+  const bool q19 = q == 19;
+  switch (precision) {
+    case FSL_FP64: return q19 ? launch_fp64_q19() : launch_fp64_q27();
+    case FSL_FP32: return q19 ? launch_fp32_q19() : launch_fp32_q27();
+    case FSL_MIXED_FP16: return q19 ? launch_fp16_q19() : launch_fp16_q27();
+    case FSL_MIXED_BF16: return q19 ? launch_bf16_q19() : launch_bf16_q27();
+  }
+  return nullptr;
+}
+
+}  // namespace
+
+size_t fsl::storage_bytes(int precision) {
+  return precision == FSL_FP64 ? 8 : precision == FSL_FP32 ? 4 : 2;
+}
+
+// ------------------------------------------------------------ observation kernels
+namespace {
+
+// column height at i = 0, front (j = 0 layer) and height (i = 0 column)
+__global__ void k_small_obs(Dev d, Geom g, double* out) {
+  __shared__ double shd[256];
+  __shared__ int shi[256];
+  double s = 0.0;
+  const int ncol = g.ny * g.nz;
+  for (int k = threadIdx.x; k < ncol; k += 256) s += d.phi[(long long)g.sx * k];
+  const double col = block_sum<256>(s, shd) / (double)g.nz;
+  int best = -1;
+  for (int k = threadIdx.x; k < g.nx * g.nz; k += 256) {
+    const int i = k % g.nx, kz = k / g.nx;
+    if ((d.flags[i + (long long)g.sx * g.ny * kz] & F_TYPE) == T_IF) best = max(best, i);
+  }
+  const int front = block_max<256>(best, shi) + 1;
+  best = -1;
+  for (int k = threadIdx.x; k < ncol; k += 256)
+    if ((d.flags[(long long)g.sx * k] & F_TYPE) == T_IF) best = max(best, k % g.ny);
+  const int height = block_max<256>(best, shi) + 1;
+  if (threadIdx.x == 0) {
+    out[0] = col;
+    out[1] = (double)front;
+    out[2] = (double)height;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_lost_partial(Dev d, Geom g, double* part) {
+  __shared__ double sh[256];
+  double s = 0.0;
+  for (long long c = blockIdx.x * 256ll + threadIdx.x; c < g.cells; c += (long long)gridDim.x * 256)
+    if ((int)(c % g.sx) < g.nx) s += d.lost[c];
+  const double b = block_sum<256>(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+__global__ void k_set_trace(Ctrl* ctrl, int every) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctrl->trace_every = every;
+    ctrl->trace_count = 0;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ handle
+struct fsl_handle {
+  fsl_config cfg;
+  Geom g;
+  Phys p;
+  Dev d;
+  const Launch* L;
+  cudaStream_t stream;
+  size_t bytes;
+  size_t off[R_COUNT];
+  bool ready;
+  int trace_every;
+  std::map<int, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+fsl_status read_ctrl(fsl_handle* h, Ctrl* c) {
+  FSL_CK(cudaMemcpyAsync(c, h->d.ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, h->stream));
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  return FSL_OK;
+}
+
+fsl_status copy_field(fsl_handle* h, const void* dev, size_t elem, void* host) {
+  // padded rows (pitch sx) -> dense host rows (nx)
+  FSL_CK(cudaMemcpy2DAsync(host, (size_t)h->g.nx * elem, dev, (size_t)h->g.sx * elem,
+                           (size_t)h->g.nx * elem, (size_t)h->g.ny * h->g.nz,
+                           cudaMemcpyDeviceToHost, h->stream));
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  return FSL_OK;
+}
+
+const size_t kGraphChunk = 64;
+
+}  // namespace
+
+extern "C" {
+
+fsl_status fsl_workspace_bytes(const fsl_config* cfg, size_t* bytes) {
+  if (!valid_config(cfg) || !bytes) return FSL_ERR_ARG;
+  Geom g;
+  make_geom(cfg, &g);
+  size_t off[R_COUNT];
+  *bytes = layout(cfg, g, off);
+  return FSL_OK;
+}
+
+fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
+                      fsl_handle** out) {
+  if (!out) return FSL_ERR_ARG;
+  *out = nullptr;
+  if (!valid_config(cfg)) return FSL_ERR_ARG;
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return FSL_ERR_WORKSPACE;
+  const Launch* L = pick(cfg->precision, cfg->lattice);
+  if (!L) return FSL_ERR_ARG;
+  fsl_handle* h = new (std::nothrow) fsl_handle();
+  if (!h) return FSL_ERR_ARG;
+  h->cfg = *cfg;
+  make_geom(cfg, &h->g);
+  make_phys(cfg, &h->p);
+  h->bytes = layout(cfg, h->g, h->off);
+  if (bytes < h->bytes) {
+    delete h;
+    return FSL_ERR_WORKSPACE;
+  }
+  char* base = static_cast<char*>(d_workspace);
+  Dev& d = h->d;
+  d.pdf[0] = base + h->off[R_PDF0];
+  d.pdf[1] = base + h->off[R_PDF1];
+  d.flags = reinterpret_cast<uint8_t*>(base + h->off[R_FLAGS]);
+  d.claim = reinterpret_cast<uint8_t*>(base + h->off[R_CLAIM]);
+  d.phi = reinterpret_cast<double*>(base + h->off[R_PHI]);
+  d.phinew = reinterpret_cast<double*>(base + h->off[R_PHINEW]);
+  d.mass = reinterpret_cast<double*>(base + h->off[R_MASS]);
+  d.rho = reinterpret_cast<double*>(base + h->off[R_RHO]);
+  d.kappa = reinterpret_cast<double*>(base + h->off[R_KAPPA]);
+  d.mex = reinterpret_cast<double*>(base + h->off[R_MEX]);
+  d.lost = reinterpret_cast<double*>(base + h->off[R_LOST]);
+  d.l_if = reinterpret_cast<int*>(base + h->off[R_LIF]);
+  d.l_fill = reinterpret_cast<int*>(base + h->off[R_LFILL]);
+  d.l_empty = reinterpret_cast<int*>(base + h->off[R_LEMPTY]);
+  d.l_new = reinterpret_cast<int*>(base + h->off[R_LNEW]);
+  d.l_l2i = reinterpret_cast<int*>(base + h->off[R_LL2I]);
+  d.l_recv = reinterpret_cast<int*>(base + h->off[R_LRECV]);
+  d.ctrl = reinterpret_cast<Ctrl*>(base + h->off[R_CTRL]);
+  d.trace = reinterpret_cast<double*>(base + h->off[R_TRACE]);
+  d.red = reinterpret_cast<double*>(base + h->off[R_RED]);
+  d.redi = nullptr;
+  h->L = L;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->ready = false;
+  h->trace_every = 0;
+  *out = h;
+  return FSL_OK;
+}
+
+fsl_status fsl_init_fill(fsl_handle* h, const double* phi, const double* u0,
+                         const unsigned char* obstacle, double h_ref) {
+  if (!h || !phi) return FSL_ERR_ARG;
+  const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  // staging: fill level in phinew, obstacle bytes in claim, u0 in the second
+  // PDF buffer (all unpadded); the init kernels move them into place
+  FSL_CK(cudaMemcpyAsync(h->d.phinew, phi, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  if (obstacle)
+    FSL_CK(cudaMemcpyAsync(h->d.claim, obstacle, n, cudaMemcpyHostToDevice, h->stream));
+  double* su = nullptr;
+  if (u0) {
+    su = static_cast<double*>(h->d.pdf[1]);
+    FSL_CK(cudaMemcpyAsync(su, u0, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  }
+  FSL_CK(h->L->init(h->d, h->g, h->p, 0, su, obstacle ? 1 : 0, h_ref, h->stream));
+  k_set_trace<<<1, 32, 0, h->stream>>>(h->d.ctrl, h->trace_every);
+  FSL_CK(cudaGetLastError());
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  h->ready = true;
+  return FSL_OK;
+}
+
+fsl_status fsl_step(fsl_handle* h, int nsteps) {
+  if (!h || nsteps < 0) return FSL_ERR_ARG;
+  if (!h->ready) return FSL_ERR_STATE;
+  if (nsteps == 0) return FSL_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (h->stream) FSL_CK(cudaStreamIsCapturing(h->stream, &cs));
+  if (!h->stream || cs != cudaStreamCaptureStatusNone) {
+    // legacy default stream (not capturable) or a capture owned by the caller
+    for (int k = 0; k < nsteps; ++k) FSL_CK(h->L->step(h->d, h->g, h->p, h->stream));
+    return FSL_OK;
+  }
+  int left = nsteps;
+  while (left > 0) {
+    const int chunk = left >= (int)kGraphChunk ? (int)kGraphChunk : left;
+    auto it = h->graphs.find(chunk);
+    if (it == h->graphs.end()) {
+      cudaGraph_t graph;
+      FSL_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t le = cudaSuccess;
+      for (int k = 0; k < chunk && le == cudaSuccess; ++k) le = h->L->step(h->d, h->g, h->p, h->stream);
+      cudaError_t ee = cudaStreamEndCapture(h->stream, &graph);
+      if (le != cudaSuccess) return cuda_fail(le, "step launch during capture");
+      if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
+      cudaGraphExec_t exec;
+      cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+      it = h->graphs.emplace(chunk, exec).first;
+    }
+    FSL_CK(cudaGraphLaunch(it->second, h->stream));
+    left -= chunk;
+  }
+  return FSL_OK;
+}
+
+fsl_status fsl_observe(fsl_handle* h, int what, void* host_out, size_t bytes) {
+  if (!h || !host_out) return FSL_ERR_ARG;
+  if (!h->ready) return FSL_ERR_STATE;
+  const size_t n = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  const int q = h->cfg.lattice;
+  Ctrl c;
+  fsl_status st = read_ctrl(h, &c);
+  if (st != FSL_OK) return st;
+  const int cur = c.step & 1;
+  double* dout = h->d.red + 2 * kReduceBlocks;  // device result slots
+  switch (what) {
+    case FSL_OBS_TOTAL_MASS:
+    case FSL_OBS_MAX_VELOCITY:
+    case FSL_OBS_LOST_MASS: {
+      if (bytes < sizeof(double)) return FSL_ERR_ARG;
+      if (what == FSL_OBS_TOTAL_MASS) FSL_CK(h->L->total_mass(h->d, h->g, h->p, cur, dout, h->stream));
+      else if (what == FSL_OBS_MAX_VELOCITY)
+        FSL_CK(h->L->max_velocity(h->d, h->g, h->p, cur, dout, h->stream));
+      else {
+        k_lost_partial<<<kReduceBlocks, 256, 0, h->stream>>>(h->d, h->g, h->d.red);
+        k_sum_partials<<<1, 256, 0, h->stream>>>(h->d.red, kReduceBlocks, dout);
+        FSL_CK(cudaGetLastError());
+      }
+      FSL_CK(cudaMemcpyAsync(host_out, dout, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      FSL_CK(cudaStreamSynchronize(h->stream));
+      return FSL_OK;
+    }
+    case FSL_OBS_COLUMN_HEIGHT:
+    case FSL_OBS_FRONT:
+    case FSL_OBS_HEIGHT: {
+      if (bytes < sizeof(double)) return FSL_ERR_ARG;
+      k_small_obs<<<1, 256, 0, h->stream>>>(h->d, h->g, dout);
+      FSL_CK(cudaGetLastError());
+      double v[3];
+      FSL_CK(cudaMemcpyAsync(v, dout, sizeof(v), cudaMemcpyDeviceToHost, h->stream));
+      FSL_CK(cudaStreamSynchronize(h->stream));
+      const double r = what == FSL_OBS_COLUMN_HEIGHT ? v[0] : what == FSL_OBS_FRONT ? v[1] : v[2];
+      std::memcpy(host_out, &r, sizeof(double));
+      return FSL_OK;
+    }
+    case FSL_OBS_STATUS: {
+      if (bytes < 2 * sizeof(int64_t)) return FSL_ERR_ARG;
+      int64_t v[2] = {c.unstable_step >= 0 ? (int64_t)FSL_ERR_UNSTABLE
+                                           : (c.timeout ? (int64_t)FSL_ERR_TIMEOUT : 0),
+                      (int64_t)c.unstable_step};
+      std::memcpy(host_out, v, sizeof(v));
+      return FSL_OK;
+    }
+    case FSL_OBS_STEP: {
+      if (bytes < sizeof(int64_t)) return FSL_ERR_ARG;
+      int64_t v = c.step;
+      std::memcpy(host_out, &v, sizeof(v));
+      return FSL_OK;
+    }
+    case FSL_OBS_COUNTS: {
+      if (bytes < 4 * sizeof(int64_t)) return FSL_ERR_ARG;
+      int64_t v[4] = {c.last[0], c.last[1], c.last[2], c.last[3]};
+      std::memcpy(host_out, v, sizeof(v));
+      return FSL_OK;
+    }
+    case FSL_OBS_TRACE: {
+      const int cnt = c.trace_count < kTraceCapacity ? c.trace_count : kTraceCapacity;
+      if (bytes < (size_t)cnt * 3 * sizeof(double)) return FSL_ERR_ARG;
+      std::vector<double> ring((size_t)kTraceCapacity * 3);
+      FSL_CK(cudaMemcpyAsync(ring.data(), h->d.trace, ring.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+      FSL_CK(cudaStreamSynchronize(h->stream));
+      const int first = c.trace_count - cnt;
+      double* o = static_cast<double*>(host_out);
+      for (int k = 0; k < cnt; ++k) {
+        const int slot = (first + k) % kTraceCapacity;
+        for (int j = 0; j < 3; ++j) o[3 * k + j] = ring[3 * slot + j];
+      }
+      return FSL_OK;
+    }
+    case FSL_OBS_FIELD_PDF: {
+      if (bytes < (size_t)q * n * sizeof(double)) return FSL_ERR_ARG;
+      double* o = static_cast<double*>(host_out);
+      for (int i = 0; i < q; ++i) {
+        FSL_CK(h->L->export_pdf(h->d, h->g, h->p, cur, i, h->d.phinew, h->stream));
+        FSL_CK(cudaMemcpyAsync(o + (size_t)i * n, h->d.phinew, n * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
+      }
+      FSL_CK(cudaStreamSynchronize(h->stream));
+      return FSL_OK;
+    }
+    case FSL_OBS_FIELD_TYPES: {
+      if (bytes < n) return FSL_ERR_ARG;
+      st = copy_field(h, h->d.flags, 1, host_out);
+      if (st != FSL_OK) return st;
+      unsigned char* o = static_cast<unsigned char*>(host_out);
+      for (size_t k = 0; k < n; ++k) o[k] &= F_TYPE;
+      return FSL_OK;
+    }
+    case FSL_OBS_FIELD_PHI:
+      if (bytes < n * sizeof(double)) return FSL_ERR_ARG;
+      return copy_field(h, h->d.phi, sizeof(double), host_out);
+    case FSL_OBS_FIELD_MASS:
+      if (bytes < n * sizeof(double)) return FSL_ERR_ARG;
+      return copy_field(h, h->d.mass, sizeof(double), host_out);
+    case FSL_OBS_FIELD_KAPPA:
+      if (bytes < n * sizeof(double)) return FSL_ERR_ARG;
+      return copy_field(h, h->d.kappa, sizeof(double), host_out);
+  }
+  return FSL_ERR_ARG;
+}
+
+fsl_status fsl_set_trace(fsl_handle* h, int every) {
+  if (!h || every < 0) return FSL_ERR_ARG;
+  h->trace_every = every;
+  if (h->ready) {
+    k_set_trace<<<1, 32, 0, h->stream>>>(h->d.ctrl, every);
+    FSL_CK(cudaGetLastError());
+  }
+  return FSL_OK;
+}
+
+int fsl_trace_capacity(void) { return kTraceCapacity; }
+
+// checkpoint: current PDF buffer, flags, phi, mass, kappa, lost, control block
+fsl_status fsl_state_bytes(const fsl_handle* h, size_t* bytes) {
+  if (!h || !bytes) return FSL_ERR_ARG;
+  size_t sz[R_COUNT];
+  region_sizes(&h->cfg, h->g, sz);
+  *bytes = sz[R_PDF0] + sz[R_FLAGS] + sz[R_PHI] + sz[R_MASS] + sz[R_KAPPA] + sz[R_LOST] + sizeof(Ctrl);
+  return FSL_OK;
+}
+
+static fsl_status state_parts(fsl_handle* h, int cur, std::vector<std::pair<char*, size_t>>& parts) {
+  size_t sz[R_COUNT];
+  region_sizes(&h->cfg, h->g, sz);
+  parts.clear();
+  parts.push_back({static_cast<char*>(h->d.pdf[cur]), sz[R_PDF0]});
+  parts.push_back({reinterpret_cast<char*>(h->d.flags), sz[R_FLAGS]});
+  parts.push_back({reinterpret_cast<char*>(h->d.phi), sz[R_PHI]});
+  parts.push_back({reinterpret_cast<char*>(h->d.mass), sz[R_MASS]});
+  parts.push_back({reinterpret_cast<char*>(h->d.kappa), sz[R_KAPPA]});
+  parts.push_back({reinterpret_cast<char*>(h->d.lost), sz[R_LOST]});
+  return FSL_OK;
+}
+
+fsl_status fsl_save(fsl_handle* h, void* host_dst, size_t bytes) {
+  if (!h || !host_dst) return FSL_ERR_ARG;
+  if (!h->ready) return FSL_ERR_STATE;
+  size_t need;
+  fsl_state_bytes(h, &need);
+  if (bytes < need) return FSL_ERR_ARG;
+  Ctrl c;
+  fsl_status st = read_ctrl(h, &c);
+  if (st != FSL_OK) return st;
+  std::vector<std::pair<char*, size_t>> parts;
+  state_parts(h, c.step & 1, parts);
+  char* o = static_cast<char*>(host_dst);
+  for (auto& pr : parts) {
+    FSL_CK(cudaMemcpyAsync(o, pr.first, pr.second, cudaMemcpyDeviceToHost, h->stream));
+    o += pr.second;
+  }
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  std::memcpy(o, &c, sizeof(Ctrl));
+  return FSL_OK;
+}
+
+fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
+  if (!h || !host_src) return FSL_ERR_ARG;
+  size_t need;
+  fsl_state_bytes(h, &need);
+  if (bytes < need) return FSL_ERR_ARG;
+  Ctrl c;
+  std::memcpy(&c, static_cast<const char*>(host_src) + need - sizeof(Ctrl), sizeof(Ctrl));
+  if (c.step < 0) return FSL_ERR_ARG;
+  std::vector<std::pair<char*, size_t>> parts;
+  state_parts(h, c.step & 1, parts);
+  const char* s = static_cast<const char*>(host_src);
+  for (auto& pr : parts) {
+    FSL_CK(cudaMemcpyAsync(pr.first, s, pr.second, cudaMemcpyHostToDevice, h->stream));
+    s += pr.second;
+  }
+  // per-step scratch restarts empty: counters zero, claim bytes zero
+  c.n_if = c.n_fill = c.n_empty = c.n_new = c.n_l2i = c.n_recv = 0;
+  c.pad[0] = 0;
+  c.trace_every = h->trace_every;
+  c.trace_count = 0;
+  FSL_CK(cudaMemcpyAsync(h->d.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
+  FSL_CK(cudaMemsetAsync(h->d.claim, 0, (size_t)h->g.cells, h->stream));
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  h->ready = true;
+  return FSL_OK;
+}
+
+fsl_status fsl_destroy(fsl_handle* h) {
+  if (!h) return FSL_ERR_ARG;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  delete h;
+  return FSL_OK;
+}
+
+fsl_status fsl_lattice_table(int lattice, int* c3q, double* w) {
+  if (lattice != FSL_D3Q19 && lattice != FSL_D3Q27) return FSL_ERR_ARG;
+  for (int i = 0; i < lattice; ++i) {
+    for (int a = 0; a < 3; ++a)
+      if (c3q) c3q[3 * i + a] = dir_c(i, a);
+    if (w) w[i] = lattice == 19 ? wgt<19>(i) : wgt<27>(i);
+  }
+  return FSL_OK;
+}
+
+int fsl_launches_per_step(const fsl_handle* h) { return h ? h->L->launches_per_step : 0; }
+
+const char* fsl_status_string(fsl_status s) {
+  switch (s) {
+    case FSL_OK: return "ok";
+    case FSL_ERR_ARG: return "invalid argument";
+    case FSL_ERR_CUDA: return "CUDA runtime error";
+    case FSL_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case FSL_ERR_UNSTABLE: return "unstable: |u| >= c_s or NaN";
+    case FSL_ERR_TIMEOUT: return "bounded device wait gave up";
+    case FSL_ERR_STATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* fsl_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,123 @@
+// Internal declarations shared by the host ABI (fsl_api.cu) and the kernel
+// translation units (one per precision family).  Not installed; the public
+// interface is include/fsl.h.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fsl {
+
+// Cell-type codes (low two bits of the flag byte).
+enum : uint8_t { T_GAS = 0, T_IF = 1, T_LIQ = 2, T_OBST = 3 };
+// Flag bits above the type.
+enum : uint8_t {
+  F_TYPE = 3,
+  F_NF = 4,        // interface cell without liquid neighbour (Thuerey class)
+  F_NE = 8,        // interface cell without gas neighbour
+  F_TO_LIQ = 16,   // fill level above 1 + eps this step (converts to liquid)
+  F_TO_GAS = 32,   // fill level below -eps this step (converts to gas)
+  F_NEW = 64,      // gas cell that became interface this step (to be refilled)
+  F_NEAR_OBST = 128  // some stencil neighbour is a wall or obstacle (static)
+};
+
+// Device control block (one per handle, in the workspace).
+struct Ctrl {
+  int step;            // steps completed
+  int unstable_step;   // first step with |u| >= c_s or NaN, -1 if none
+  unsigned n_if;       // interface cells seen by the stream-collide pass
+  unsigned n_fill;     // cells marked to fill
+  unsigned n_empty;    // cells marked to empty
+  unsigned n_new;      // gas -> interface cells
+  unsigned n_l2i;      // liquid -> interface cells
+  unsigned n_recv;     // excess-mass receivers
+  unsigned last[4];    // previous step: filled, emptied (after conflicts), new, interface
+  int trace_every;     // 0: no trace
+  int trace_count;     // records written (ring index = count % capacity)
+  unsigned timeout;    // bounded-wait error flag (never set by the step kernels)
+  unsigned pad[3];
+};
+
+constexpr int kTraceCapacity = 1 << 16;
+constexpr int kListBlocks = 2 * 152;  // grid of the list-driven kernels
+constexpr int kReduceBlocks = 4 * 152;
+
+struct Geom {
+  int nx, ny, nz;
+  int sx;              // padded row stride (elements/cells)
+  long long cells;     // padded cell count nz*ny*sx
+  long long plane;     // PDF plane stride in elements (>= cells, 128-element multiple)
+  int periodic[3];
+};
+
+struct Phys {
+  int q;
+  int trt;
+  int refill;
+  unsigned options;
+  double tau, omega, lam_e, lam_o;  // SRT omega; TRT even/odd rates
+  double pre_e, pre_o;              // 1 - lam/2 Guo prefactors (pre_e also SRT)
+  double g[3];
+  int gaxis;                        // last axis with nonzero g, -1 if none
+  double sigma, p_v, eps;
+  double geq_coef;                  // 1/(2 c_s^2 omega) = 1.5 tau, or 1.5/nu
+  double thr_hi, thr_lo;            // 1 + eps, 0 - eps
+};
+
+struct Dev {
+  void* pdf[2];       // ping-pong PDF buffers (storage type of the precision)
+  uint8_t* flags;
+  uint8_t* claim;     // receiver claim bytes (zero between steps)
+  double* phi;        // fill level
+  double* phinew;     // fill level computed by stream-collide (interface cells)
+  double* mass;       // cell mass (interface cells)
+  double* rho;        // density recorded this step (interface cells)
+  double* kappa;      // curvature K (interface cells)
+  double* mex;        // excess mass of converted cells / share per receiver
+  double* lost;       // per-cell lost excess mass (no receiver)
+  int* l_if;
+  int* l_fill;
+  int* l_empty;
+  int* l_new;
+  int* l_l2i;
+  int* l_recv;
+  Ctrl* ctrl;
+  double* trace;      // kTraceCapacity * 3 doubles
+  double* red;        // reduction scratch, kReduceBlocks * 2 doubles
+  int* redi;          // integer reduction scratch
+};
+
+// Per-precision-family launch table, implemented in fsl_prec_*.cu.
+struct Launch {
+  // one full time step from pdf[step & 1] to pdf[(step + 1) & 1]
+  cudaError_t (*step)(const Dev&, const Geom&, const Phys&, cudaStream_t);
+  // initial state into pdf[cur] (cur = 0); staged: fill level in d.phinew and
+  // obstacle bytes in d.claim (both unpadded), u0 (3N doubles, unpadded) in
+  // stage_u or null
+  cudaError_t (*init)(const Dev&, const Geom&, const Phys&, int cur, const double* stage_u,
+                      int have_obstacle, double h_ref, cudaStream_t);
+  // total mass (fluid zeroth moments + interface m + lost) into out (device double)
+  cudaError_t (*total_mass)(const Dev&, const Geom&, const Phys&, int cur, double* out,
+                            cudaStream_t);
+  // max |u| over fluid cells into out (device double)
+  cudaError_t (*max_velocity)(const Dev&, const Geom&, const Phys&, int cur, double* out,
+                              cudaStream_t);
+  // decode plane i of pdf[cur] into dst (device, nx*ny*nz doubles, unpadded)
+  cudaError_t (*export_pdf)(const Dev&, const Geom&, const Phys&, int cur, int i, double* dst,
+                            cudaStream_t);
+  int launches_per_step;
+};
+
+// Launch tables, one translation unit per (storage, lattice).
+const Launch* launch_fp64_q19();
+const Launch* launch_fp64_q27();
+const Launch* launch_fp32_q19();
+const Launch* launch_fp32_q27();
+const Launch* launch_fp16_q19();
+const Launch* launch_fp16_q27();
+const Launch* launch_bf16_q19();
+const Launch* launch_bf16_q27();
+
+size_t storage_bytes(int precision);
+
+}  // namespace fsl

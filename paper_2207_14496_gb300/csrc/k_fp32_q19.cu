@@ -1,0 +1,8 @@
+// Step kernels instantiated for storage fp32, D3Q19.
+// FP32 arithmetic on offsets f_i - w_i; cell mass, excess mass and reductions
+// stay FP64.
+#include "fsl_kernels.cuh"
+
+namespace fsl {
+const Launch* launch_fp32_q19() { return Kernels<19, SF32>::table(); }
+}  // namespace fsl

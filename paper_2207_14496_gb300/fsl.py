@@ -1,0 +1,296 @@
+"""Thin Python binding of libfsl (C ABI in include/fsl.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides the device workspace (one uint8 tensor) and
+the CUDA stream.  Importing this module loads ``_build/libfsl.so`` and raises
+if it has not been built; there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfsl.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"libfsl.so not found at {LIB_PATH}; build it with "
+        "`python -m paper_2207_14496_gb300.build` (or __graft_entry__.build())")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+D3Q19, D3Q27 = 19, 27
+SRT, TRT = 0, 1
+FP64, FP32, MIXED_FP16, MIXED_BF16 = 0, 1, 2, 3
+PRECISIONS = {"fp64": FP64, "fp32": FP32, "fp16": MIXED_FP16, "bf16": MIXED_BF16}
+REFILL = {"eq": 0, "eq_neq": 1, "geq": 2, "ext": 3, "avg": 4}
+OPT_SIMPLE_FLUX, OPT_GEQ_LITERAL_NU, OPT_NEQ_LITERAL_MEAN, OPT_LAPLACE_LITERAL = 1, 2, 4, 8
+
+OBS_TOTAL_MASS, OBS_COLUMN_HEIGHT, OBS_FRONT, OBS_HEIGHT = 1, 2, 3, 4
+OBS_MAX_VELOCITY, OBS_STATUS, OBS_STEP, OBS_COUNTS = 5, 6, 7, 8
+OBS_LOST_MASS, OBS_TRACE = 9, 10
+OBS_FIELD_PDF, OBS_FIELD_TYPES, OBS_FIELD_PHI, OBS_FIELD_MASS, OBS_FIELD_KAPPA = 16, 17, 18, 19, 20
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace", -4: "unstable",
+          -5: "timeout", -6: "state"}
+ERR_UNSTABLE = -4
+
+
+class fsl_config(ctypes.Structure):
+    _fields_ = [
+        ("lattice", ctypes.c_int),
+        ("collision", ctypes.c_int),
+        ("trt_magic", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("refill", ctypes.c_int),
+        ("nx", ctypes.c_int),
+        ("ny", ctypes.c_int),
+        ("nz", ctypes.c_int),
+        ("periodic", ctypes.c_int * 3),
+        ("nu", ctypes.c_double),
+        ("gravity", ctypes.c_double * 3),
+        ("sigma", ctypes.c_double),
+        ("p_volume", ctypes.c_double),
+        ("eps_phi", ctypes.c_double),
+        ("options", ctypes.c_uint),
+    ]
+
+
+_VP = ctypes.c_void_p
+_SZ = ctypes.c_size_t
+_lib.fsl_workspace_bytes.argtypes = [ctypes.POINTER(fsl_config), ctypes.POINTER(_SZ)]
+_lib.fsl_create.argtypes = [ctypes.POINTER(fsl_config), _VP, _SZ, _VP, ctypes.POINTER(_VP)]
+_lib.fsl_init_fill.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_double]
+_lib.fsl_step.argtypes = [_VP, ctypes.c_int]
+_lib.fsl_observe.argtypes = [_VP, ctypes.c_int, _VP, _SZ]
+_lib.fsl_set_trace.argtypes = [_VP, ctypes.c_int]
+_lib.fsl_trace_capacity.restype = ctypes.c_int
+_lib.fsl_state_bytes.argtypes = [_VP, ctypes.POINTER(_SZ)]
+_lib.fsl_save.argtypes = [_VP, _VP, _SZ]
+_lib.fsl_load.argtypes = [_VP, _VP, _SZ]
+_lib.fsl_destroy.argtypes = [_VP]
+_lib.fsl_lattice_table.argtypes = [ctypes.c_int, _VP, _VP]
+_lib.fsl_launches_per_step.argtypes = [_VP]
+_lib.fsl_launches_per_step.restype = ctypes.c_int
+_lib.fsl_status_string.argtypes = [ctypes.c_int]
+_lib.fsl_status_string.restype = ctypes.c_char_p
+_lib.fsl_last_error.restype = ctypes.c_char_p
+for _name in ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "fsl_observe",
+              "fsl_set_trace", "fsl_state_bytes", "fsl_save", "fsl_load", "fsl_destroy",
+              "fsl_lattice_table"):
+    getattr(_lib, _name).restype = ctypes.c_int
+
+EXPORTED = ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "fsl_observe",
+            "fsl_set_trace", "fsl_trace_capacity", "fsl_state_bytes", "fsl_save", "fsl_load",
+            "fsl_destroy", "fsl_lattice_table", "fsl_launches_per_step", "fsl_status_string",
+            "fsl_last_error")
+
+
+class FslError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        msg = _lib.fsl_status_string(code).decode()
+        if code == -2:
+            msg += ": " + _lib.fsl_last_error().decode()
+        super().__init__(f"{where}: {msg} ({code})")
+        self.code = code
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise FslError(code, where)
+
+
+def make_config(params: dict, precision: str = "fp64") -> fsl_config:
+    """Build an fsl_config from a workload parameter dictionary (see inputs)."""
+    c = fsl_config()
+    c.lattice = int(params.get("q", 19))
+    c.collision = TRT if params.get("collision", "srt") == "trt" else SRT
+    c.trt_magic = float(params.get("magic", 3.0 / 16.0))
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    c.refill = REFILL[params.get("refill", "eq")]
+    c.nx, c.ny, c.nz = (int(v) for v in params["shape"])
+    per = params.get("periodic", (True, False, True))
+    for a in range(3):
+        c.periodic[a] = 1 if per[a] else 0
+    c.nu = float(params["nu"])
+    g = params.get("g", (0.0, 0.0, 0.0))
+    for a in range(3):
+        c.gravity[a] = float(g[a])
+    c.sigma = float(params.get("sigma", 0.0))
+    c.p_volume = float(params.get("p_v", 1.0 / 3.0))
+    c.eps_phi = float(params.get("eps", 1e-2))
+    c.options = int(params.get("options", 0))
+    return c
+
+
+def workspace_bytes(params: dict, precision: str = "fp64") -> int:
+    c = make_config(params, precision)
+    n = _SZ()
+    _check(_lib.fsl_workspace_bytes(ctypes.byref(c), ctypes.byref(n)), "fsl_workspace_bytes")
+    return int(n.value)
+
+
+def lattice_table(q: int):
+    c = np.zeros((q, 3), dtype=np.int32)
+    w = np.zeros(q, dtype=np.float64)
+    _check(_lib.fsl_lattice_table(q, c.ctypes.data, w.ctypes.data), "fsl_lattice_table")
+    return c, w
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Sim:
+    """One FSLBM domain on the current CUDA device.
+
+    The workspace is a torch uint8 tensor owned by this object; the stream is
+    a dedicated torch stream (so that steps can be captured into CUDA graphs)
+    unless one is passed.
+    """
+
+    def __init__(self, params: dict, precision: str = "fp64", device: int = 0, stream=None):
+        import torch
+
+        self.params = dict(params)
+        self.precision = precision
+        self.cfg = make_config(params, precision)
+        self.q = self.cfg.lattice
+        self.shape = (self.cfg.nx, self.cfg.ny, self.cfg.nz)
+        self.N = self.cfg.nx * self.cfg.ny * self.cfg.nz
+        self.device = torch.device("cuda", device)
+        n = _SZ()
+        _check(_lib.fsl_workspace_bytes(ctypes.byref(self.cfg), ctypes.byref(n)),
+               "fsl_workspace_bytes")
+        self.bytes = int(n.value)
+        self.workspace = torch.empty(self.bytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._base = (base + 255) // 256 * 256
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=self.device)
+        h = ctypes.c_void_p()
+        _check(_lib.fsl_create(ctypes.byref(self.cfg), ctypes.c_void_p(self._base), self.bytes,
+                               ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+               "fsl_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            _lib.fsl_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launches_per_step(self) -> int:
+        return int(_lib.fsl_launches_per_step(self.h))
+
+    def init_fill(self, phi, u0=None, obstacle=None, h_ref=float("nan")):
+        phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(-1))
+        assert phi.size == self.N
+        keep = [phi]
+        up = None
+        if u0 is not None:
+            u0 = np.ascontiguousarray(np.asarray(u0, dtype=np.float64).reshape(-1))
+            assert u0.size == 3 * self.N
+            keep.append(u0)
+            up = _ptr(u0)
+        op = None
+        if obstacle is not None:
+            obstacle = np.ascontiguousarray(np.asarray(obstacle, dtype=np.uint8).reshape(-1))
+            keep.append(obstacle)
+            op = _ptr(obstacle)
+        _check(_lib.fsl_init_fill(self.h, _ptr(phi), up, op, float(h_ref)), "fsl_init_fill")
+
+    def init_workload(self, w: dict):
+        self.init_fill(w["phi"], w.get("u0"), w.get("obstacle"), w.get("h_ref", float("nan")))
+
+    def step(self, n: int = 1):
+        _check(_lib.fsl_step(self.h, int(n)), "fsl_step")
+
+    def set_trace(self, every: int):
+        _check(_lib.fsl_set_trace(self.h, int(every)), "fsl_set_trace")
+
+    # -- observation ------------------------------------------------------------
+    def _obs(self, what: int, out: np.ndarray):
+        _check(_lib.fsl_observe(self.h, what, _ptr(out), out.nbytes), f"fsl_observe({what})")
+        return out
+
+    def _scalar(self, what):
+        return float(self._obs(what, np.zeros(1))[0])
+
+    def total_mass(self):
+        return self._scalar(OBS_TOTAL_MASS)
+
+    def column_height(self):
+        return self._scalar(OBS_COLUMN_HEIGHT)
+
+    def front(self):
+        return self._scalar(OBS_FRONT)
+
+    def height(self):
+        return self._scalar(OBS_HEIGHT)
+
+    def max_velocity(self):
+        return self._scalar(OBS_MAX_VELOCITY)
+
+    def lost_mass(self):
+        return self._scalar(OBS_LOST_MASS)
+
+    def status(self):
+        v = self._obs(OBS_STATUS, np.zeros(2, dtype=np.int64))
+        return int(v[0]), int(v[1])
+
+    @property
+    def step_count(self) -> int:
+        return int(self._obs(OBS_STEP, np.zeros(1, dtype=np.int64))[0])
+
+    def counts(self):
+        return tuple(int(v) for v in self._obs(OBS_COUNTS, np.zeros(4, dtype=np.int64)))
+
+    def trace(self, n: int):
+        out = np.zeros((n, 3))
+        _check(_lib.fsl_observe(self.h, OBS_TRACE, _ptr(out), out.nbytes), "fsl_observe(trace)")
+        return out
+
+    def _grid(self):
+        nx, ny, nz = self.shape
+        return (nz, ny, nx)
+
+    def pdfs(self):
+        return self._obs(OBS_FIELD_PDF, np.zeros(self.q * self.N)).reshape((self.q,) + self._grid())
+
+    def types(self):
+        return self._obs(OBS_FIELD_TYPES, np.zeros(self.N, dtype=np.uint8)).reshape(self._grid())
+
+    def phi(self):
+        return self._obs(OBS_FIELD_PHI, np.zeros(self.N)).reshape(self._grid())
+
+    def mass(self):
+        return self._obs(OBS_FIELD_MASS, np.zeros(self.N)).reshape(self._grid())
+
+    def kappa(self):
+        return self._obs(OBS_FIELD_KAPPA, np.zeros(self.N)).reshape(self._grid())
+
+    # -- checkpoint -------------------------------------------------------------
+    def save(self) -> np.ndarray:
+        n = _SZ()
+        _check(_lib.fsl_state_bytes(self.h, ctypes.byref(n)), "fsl_state_bytes")
+        buf = np.zeros(int(n.value), dtype=np.uint8)
+        _check(_lib.fsl_save(self.h, _ptr(buf), buf.nbytes), "fsl_save")
+        return buf
+
+    def load(self, buf: np.ndarray):
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(_lib.fsl_load(self.h, _ptr(buf), buf.nbytes), "fsl_load")
+
+
+def raw_library():
+    """The loaded ctypes library (for the C-ABI symbol checks)."""
+    return _lib

@@ -1,0 +1,199 @@
+"""Seeded synthetic inputs: initial fill levels, velocities and parameter sets.
+
+This module holds geometry and parameter recipes only -- none of the method's
+arithmetic.  Both the CUDA library (through its Python binding) and the CPU
+oracle consume what it returns, so each workload is defined exactly once.
+
+Geometry conventions (reading R13):
+  * arrays are (nz, ny, nx), x fastest;
+  * for the wave, cell i covers x in [i - 1/2, i + 1/2) so that column 0 is
+    centred on x = 0, and cell j covers y in [j, j + 1) above the bottom wall;
+  * elsewhere cell (i, j, k) covers [i, i+1) x [j, j+1) x [k, k+1);
+  * walls are a virtual obstacle layer outside the stated domain size.
+
+The workloads restate the paper's experiments in shape (standing gravity wave,
+Sec. 4.1; rectangular dam break, Sec. 4.2; drop impact, Sec. 4.5) at the sizes
+used for parity and measurement.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+REFILL_SCHEMES = ("eq", "eq_neq", "geq", "ext", "avg")
+
+
+# ----------------------------------------------------------------- geometry
+def wave_fill(nx: int, ny: int, nz: int, depth: float, amp: float, wavelength: float,
+              perturb=None) -> np.ndarray:
+    """Fill level of h(x) = depth + amp cos(2 pi x / wavelength) (+ perturb[i]).
+
+    phi(i, j) is the cell average over x of clamp(h(x) - j, 0, 1), taken with
+    64-point Gauss-Legendre quadrature; perturb (length nx, cells) shifts the
+    surface of column i uniformly.
+    """
+    xg, wg = np.polynomial.legendre.leggauss(64)
+    k = 2.0 * math.pi / wavelength
+    i = np.arange(nx, dtype=np.float64)
+    xs = i[:, None] + 0.5 * xg[None, :]                      # (nx, 64)
+    h = depth + amp * np.cos(k * xs)
+    if perturb is not None:
+        h = h + np.asarray(perturb, dtype=np.float64)[:, None]
+    j = np.arange(ny, dtype=np.float64)
+    frac = np.clip(h[None, :, :] - j[:, None, None], 0.0, 1.0)  # (ny, nx, 64)
+    phi2 = 0.5 * np.tensordot(frac, wg, axes=([2], [0]))        # (ny, nx)
+    phi2 = np.where(phi2 > 1.0 - 1e-15, 1.0, phi2)
+    phi2 = np.where(phi2 < 1e-15, 0.0, phi2)
+    return np.ascontiguousarray(np.broadcast_to(phi2, (nz, ny, nx)))
+
+
+def box_fill(nx: int, ny: int, nz: int, width: int, height: int) -> np.ndarray:
+    """Liquid column occupying cells i < width, j < height (all k)."""
+    phi = np.zeros((nz, ny, nx))
+    phi[:, :height, :width] = 1.0
+    return phi
+
+
+def sphere_fraction(nx: int, ny: int, nz: int, centre, radius: float, sub: int = 8):
+    """Volume fraction of a sphere in each cell, sub^3 samples per cut cell."""
+    cx, cy, cz = centre
+    frac = np.zeros((nz, ny, nx))
+    lo = [max(0, int(math.floor(c - radius)) - 1) for c in (cx, cy, cz)]
+    hi = [min(n, int(math.ceil(c + radius)) + 2) for c, n in zip((cx, cy, cz), (nx, ny, nz))]
+    ks = np.arange(lo[2], hi[2])
+    js = np.arange(lo[1], hi[1])
+    is_ = np.arange(lo[0], hi[0])
+    K, J, I = np.meshgrid(ks, js, is_, indexing="ij")
+    # distance from the cell centre: classify cells entirely in or out
+    d = np.sqrt((I + 0.5 - cx) ** 2 + (J + 0.5 - cy) ** 2 + (K + 0.5 - cz) ** 2)
+    half_diag = math.sqrt(3.0) / 2.0
+    inside = d <= radius - half_diag
+    cut = (~inside) & (d < radius + half_diag)
+    block = np.where(inside, 1.0, 0.0)
+    off = (np.arange(sub) + 0.5) / sub
+    ox, oy, oz = np.meshgrid(off, off, off, indexing="ij")
+    ox, oy, oz = ox.ravel(), oy.ravel(), oz.ravel()
+    kk, jj, ii = np.nonzero(cut)
+    for t in range(0, kk.size, 4096):
+        k_ = K[kk[t:t + 4096], jj[t:t + 4096], ii[t:t + 4096]][:, None]
+        j_ = J[kk[t:t + 4096], jj[t:t + 4096], ii[t:t + 4096]][:, None]
+        i_ = I[kk[t:t + 4096], jj[t:t + 4096], ii[t:t + 4096]][:, None]
+        r2 = (i_ + ox - cx) ** 2 + (j_ + oy - cy) ** 2 + (k_ + oz - cz) ** 2
+        block[kk[t:t + 4096], jj[t:t + 4096], ii[t:t + 4096]] = (r2 <= radius * radius).mean(axis=1)
+    frac[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]] = block
+    return frac
+
+
+def cylinder_fraction(nx: int, ny: int, centre, radius: float, sub: int = 16):
+    """Area fraction of a disc in each cell of an nx x ny layer (nz = 1)."""
+    cx, cy = centre
+    off = (np.arange(sub) + 0.5) / sub
+    J, I = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    acc = np.zeros((ny, nx))
+    for oy in off:
+        for ox in off:
+            acc += ((I + ox - cx) ** 2 + (J + oy - cy) ** 2 <= radius * radius)
+    return (acc / (sub * sub))[None, :, :]
+
+
+# ----------------------------------------------------------------- workloads
+def _base(**kw):
+    p = dict(q=19, collision="srt", magic=3.0 / 16.0, refill="eq", periodic=(True, False, True),
+             nu=0.01, g=(0.0, 0.0, 0.0), sigma=0.0, p_v=1.0 / 3.0, eps=1e-2, options=0)
+    p.update(kw)
+    return p
+
+
+def standing_wave(L: int = 64, nz: int = 1, depth=None, amp=None, nu: float = 0.01,
+                  g: float = 1e-5, refill: str = "eq", q: int = 19, collision: str = "srt",
+                  perturb=None, ny=None):
+    """Standing gravity wave (Sec. 4.1): L x L x nz, periodic x and z, no-slip y
+    walls, depth L/2, amplitude 0.01 L, wavelength L, gravity -y."""
+    depth = L / 2 if depth is None else depth
+    amp = 0.01 * L if amp is None else amp
+    ny = L if ny is None else ny
+    params = _base(q=q, collision=collision, refill=refill, shape=(L, ny, nz),
+                   periodic=(True, False, True), nu=nu, g=(0.0, -g, 0.0))
+    phi = wave_fill(L, ny, nz, depth, amp, L, perturb)
+    return dict(name=f"standing_wave_{L}x{ny}x{nz}", params=params, phi=phi, u0=None,
+                obstacle=None, h_ref=float(depth), depth=float(depth), amp=float(amp),
+                wavelength=float(L))
+
+
+def dam_break(nx=512, ny=256, nz=16, width=128, height=128, g=2e-5, nu=5e-4,
+              refill="eq", q=19, collision="trt"):
+    """Rectangular dam break (Sec. 4.2 in shape): column width x height at the
+    left wall, no-slip walls on all faces, gravity -y, TRT with Lambda = 3/16."""
+    params = _base(q=q, collision=collision, refill=refill, shape=(nx, ny, nz),
+                   periodic=(False, False, False), nu=nu, g=(0.0, -g, 0.0))
+    phi = box_fill(nx, ny, nz, width, height)
+    return dict(name=f"dam_break_{nx}x{ny}x{nz}", params=params, phi=phi, u0=None,
+                obstacle=None, h_ref=float(height), width=width, height=height)
+
+
+def drop_impact(n=256, pool=96, diameter=40.0, gap=30.0, speed=0.05, sigma=1e-4, g=1e-6,
+                nu=5e-4, refill="eq", q=27, collision="trt", nxy=None):
+    """Drop impact into a pool (Sec. 4.5 in shape): n^3 (or nxy x nxy x n),
+    periodic x and y, no-slip z walls, pool depth `pool`, drop of the given
+    diameter centred `gap` cells above the surface, moving at -speed in z."""
+    nxy = n if nxy is None else nxy
+    params = _base(q=q, collision=collision, refill=refill, shape=(nxy, nxy, n),
+                   periodic=(True, True, False), nu=nu, g=(0.0, 0.0, -g), sigma=sigma)
+    phi = np.zeros((n, nxy, nxy))
+    phi[:pool] = 1.0
+    centre = (nxy / 2.0, nxy / 2.0, pool + gap)
+    drop = sphere_fraction(nxy, nxy, n, centre, diameter / 2.0)
+    phi = np.maximum(phi, drop)
+    u0 = np.zeros((n, nxy, nxy, 3))
+    u0[..., 2] = np.where(drop > 0.0, -speed, 0.0)
+    return dict(name=f"drop_impact_{nxy}x{nxy}x{n}", params=params, phi=phi, u0=u0,
+                obstacle=None, h_ref=float(pool))
+
+
+def static_drop(n=32, radius=8.0, sigma=1e-3, nu=0.1, q=19, two_d=False):
+    """Resting drop in a fully periodic box without gravity (Young-Laplace)."""
+    if two_d:
+        params = _base(q=q, shape=(n, n, 1), periodic=(True, True, True), nu=nu, sigma=sigma)
+        phi = cylinder_fraction(n, n, (n / 2.0, n / 2.0), radius)
+    else:
+        params = _base(q=q, shape=(n, n, n), periodic=(True, True, True), nu=nu, sigma=sigma)
+        phi = sphere_fraction(n, n, n, (n / 2.0, n / 2.0, n / 2.0), radius)
+    return dict(name=f"static_drop_{n}", params=params, phi=phi, u0=None, obstacle=None,
+                h_ref=float("nan"), radius=radius)
+
+
+def poiseuille(ny=16, nx=4, g=1e-6, nu=0.1, collision="trt", q=19):
+    """Fully liquid channel between no-slip walls at y = 0 and y = ny, driven by
+    a body force along x (no interface)."""
+    params = _base(q=q, collision=collision, shape=(nx, ny, 1), periodic=(True, False, True),
+                   nu=nu, g=(g, 0.0, 0.0))
+    phi = np.ones((1, ny, nx))
+    return dict(name=f"poiseuille_{ny}", params=params, phi=phi, u0=None, obstacle=None,
+                h_ref=float("nan"))
+
+
+def batched_waves(seed: int = 2207, n_geom: int = 64):
+    """Geometries of the batched standing-wave set: wavelength U[32, 256],
+    width U{1..8}, depth = wavelength/2, amplitude 1% of the wavelength,
+    viscosity U[1e-3, 1e-2], gravity 1e-5; each geometry times five schemes."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for gi in range(n_geom):
+        lam = int(round(rng.uniform(32.0, 256.0)))
+        width = int(rng.integers(1, 9))
+        nu = float(rng.uniform(1e-3, 1e-2))
+        for scheme in REFILL_SCHEMES:
+            out.append(dict(lam=lam, width=width, nu=nu, refill=scheme, geom=gi))
+    return out
+
+
+def workload(name: str, **kw):
+    """Named workloads at the sizes quoted for them."""
+    if name == "standing_wave_64":
+        return standing_wave(64, **kw)
+    if name == "dam_break_512":
+        return dam_break(**kw)
+    if name == "drop_impact_256":
+        return drop_impact(**kw)
+    raise KeyError(name)
