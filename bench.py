@@ -1,0 +1,336 @@
+"""Benchmark of the free-surface LBM step on one GB300 (or N replicas).
+
+Workload: the drop impact into a pool, 256^3 cells, D3Q27 TRT (Lambda 3/16),
+surface tension 1e-4, gravity 1e-6, EQ refilling (Sec. 4.5 in shape), with
+seeded synthetic initial fill levels.  The metric is MLUPS (all lattice cells
+per second) of the whole step (stream-collide, interface pass, conversion,
+refilling, excess mass, curvature, per-step observables), mixed precision
+(FP16 offset storage, FP32 collide) as the headline, with FP32 and FP64 (and
+BF16) on the same workload beside it, and the HBM-roofline fraction of the
+dominant kernel.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) each rank runs an independent replica of the domain
+(the step has no exchange between independent domains); value sums all ranks.
+`--impl reference` times the CPU oracle (the only reference implementation of
+this method here) on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+WORKLOAD = "drop_impact_256"
+METRIC = "FSLBM MLUPS (all cells), mixed FP16 vs FP64, drop impact 256^3 D3Q27"
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as fh:
+            d = json.load(fh)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), source="measured")
+    return dict(hbm_gbs=6800.0, source="fallback")
+
+
+# FP64 ALU peak for the bit-exact path, which is built without multiply-add
+# contraction (one FP64 instruction per operation): 152 SMs x 2 FP64 lanes
+# per SM per clock x 2.07 GHz (= 1.26 TFLOP/s when counted as FMA flops).
+FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while timing."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        rows = []
+        for line in (self.out or "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["unsampled"], samples=0)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k] == "Active"})
+        return dict(sm_mhz=statistics.median(sm) if sm else None,
+                    sm_max_mhz=max(smax) if smax else None, reasons=reasons, samples=len(rows))
+
+
+def time_precision(fsl, w, precision, steps, warmup, dev, barrier):
+    """Device-resident timing: CUDA events on the library's stream around K
+    steps (captured CUDA graphs), after W warm-up steps."""
+    import torch
+
+    sim = fsl.Sim(w["params"], precision, device=dev)
+    sim.init_workload(w)
+    sim.set_trace(1)
+    sim.step(warmup)
+    torch.cuda.synchronize(dev)
+    n_cells = sim.N
+    ks0 = sim.kernel_stats(reps=5)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev) as clk:
+        e0.record(sim.stream)
+        sim.step(steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize(dev)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    ks1 = sim.kernel_stats(reps=10)
+    status = sim.status()
+    launches = sim.launches_per_step() * steps
+    del sim
+    torch.cuda.empty_cache()
+    return dict(ms=ms, ms_per_step=ms / steps, mlups=n_cells * steps / (ms * 1e-3) / 1e6,
+                kernel_ms=0.5 * (ks0["ms"] + ks1["ms"]),
+                kernel_bytes=0.5 * (ks0["bytes"] + ks1["bytes"]),
+                n_liquid=0.5 * (ks0["n_liquid"] + ks1["n_liquid"]),
+                n_interface=0.5 * (ks0["n_interface"] + ks1["n_interface"]),
+                clocks=clk.summary(), status=status, launches=launches)
+
+
+def e2e_run(fsl, w, precision, steps, dev):
+    """End to end through the public API from pinned host memory: initial
+    state upload, K steps, per-step observable trace and total mass read back."""
+    import torch
+
+    sim = fsl.Sim(w["params"], precision, device=dev)
+    phi = torch.from_numpy(np.ascontiguousarray(w["phi"], dtype=np.float64)).pin_memory()
+    u0 = torch.from_numpy(np.ascontiguousarray(w["u0"], dtype=np.float64)).pin_memory()
+    phin, u0n = phi.numpy(), u0.numpy()
+    sim.set_trace(1)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    sim.init_fill(phin, u0n, None, w["h_ref"])
+    sim.step(steps)
+    trace = sim.trace(steps)
+    mass = sim.total_mass()
+    t1 = time.perf_counter()
+    del sim
+    torch.cuda.empty_cache()
+    n = int(np.prod(w["params"]["shape"]))
+    h2d = phin.nbytes + u0n.nbytes
+    d2h = trace.nbytes + 8 + 16 * 2  # trace, mass, status/step reads inside observe
+    return dict(seconds=t1 - t0, mlups=n * steps / (t1 - t0) / 1e6,
+                h2d_per_step=h2d / steps, d2h_per_step=d2h / steps, mass=mass)
+
+
+def cpu_baseline(w, steps=1):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample: the
+    full 256^3 workload for `steps` time steps (initial state untimed)."""
+    import oracle
+    o = oracle.Oracle(w["params"])
+    o.init_fill(w["phi"], w.get("u0"), None, w["h_ref"])
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    n = int(np.prod(w["params"]["shape"]))
+    return dict(value=n * steps / dt / 1e6, unit="MLUPS", cores=1, kind="oracle",
+                sample=f"{steps} step(s) of the full 256^3 D3Q27 drop-impact workload, "
+                       f"single-threaded FP64 C oracle, {dt:.1f} s")
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle, timed on the machine's host core, one oracle
+    time step per bench step on a bounded 64^3 sample of the drop impact
+    (same physics scaled down so that the whole run ends within minutes)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_2207_14496_gb300 import inputs
+    import oracle
+    w = inputs.drop_impact(n=64, pool=24, diameter=10.0, gap=8.0)
+    o = oracle.Oracle(w["params"])
+    o.init_fill(w["phi"], w.get("u0"), None, w["h_ref"])
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    n = int(np.prod(w["params"]["shape"]))
+    v = n * args.steps / dt / 1e6
+    sample = (f"64^3 D3Q27 TRT drop impact (pool 24, drop D=10), {args.steps} oracle steps "
+              f"single-threaded FP64, {dt:.1f} s")
+    line = dict(impl="reference", metric=METRIC, value=v, unit="MLUPS", n_gpus=args.gpus,
+                steps=args.steps, warmup=args.warmup, ms_per_step=dt * 1e3 / args.steps,
+                higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
+                data="synthetic", config=dict(workload=WORKLOAD, sample="64^3 scaled drop impact",
+                                              parallelism="cpu-1"),
+                cpu_baseline=dict(value=v, unit="MLUPS", cores=1, kind="oracle", sample=sample),
+                e2e=dict(value=v, unit="MLUPS", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precisions", default="fp16,fp32,fp64,bf16")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="steps for the FP64 comparison line (default: steps // 5)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2207_14496_gb300 import build, inputs
+    build.build()
+    from paper_2207_14496_gb300 import fsl
+
+    w = inputs.drop_impact()
+    peaks = load_peaks()
+    precs = [p for p in args.precisions.split(",") if p]
+    res = {}
+    for p in precs:
+        k = args.steps
+        if p == "fp64":
+            k = args.fp64_steps or max(10, args.steps // 5)
+        res[p] = time_precision(fsl, w, p, k, args.warmup, local, barrier)
+        res[p]["steps"] = k
+    head = precs[0]
+    h = res[head]
+    ms_max = max_over_ranks(h["ms"])
+    n_cells = int(np.prod(w["params"]["shape"]))
+    value = world * n_cells * h["steps"] / (ms_max * 1e-3) / 1e6
+
+    def roofline(r, prec):
+        if prec == "fp64":
+            # FP64 is bound by the FP64 pipe on GB300: algorithmic flops of the
+            # stream-collide kernel (D3Q27 TRT with Guo forcing, counted per
+            # liquid cell) over its launch time
+            flops = r["n_liquid"] * FLOPS_PER_CELL_D3Q27_TRT
+            ach = flops / (r["kernel_ms"] * 1e-3) / 1e12
+            return dict(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
+                        frac=ach / FP64_PEAK_TFLOPS, traffic=None, kernel="k_stream_collide",
+                        peak_source="152 SMs x 2 FP64 lanes/clk x 2.07 GHz, one op per instruction")
+        ach = r["kernel_bytes"] / (r["kernel_ms"] * 1e-3) / 1e9
+        return dict(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=ach / peaks["hbm_gbs"], traffic=TRAFFIC.get(prec),
+                    kernel="k_stream_collide", peak_source=peaks["source"])
+
+    by_prec = {}
+    for p in precs:
+        r = res[p]
+        by_prec[p] = dict(mlups=r["mlups"], ms_per_step=r["ms_per_step"], steps=r["steps"],
+                          kernel_ms=r["kernel_ms"], kernel_bytes=r["kernel_bytes"],
+                          roofline=roofline(r, p), status=list(r["status"]),
+                          clocks=r["clocks"])
+    # a step after a latched instability does no work: such a run is not a
+    # measurement of the step
+    unstable = {p: res[p]["status"][1] for p in precs if res[p]["status"][0] != 0}
+    e2e = None
+    if not args.no_e2e:
+        e = e2e_run(fsl, w, head, h["steps"], local)
+        e2e = dict(value=world * e["mlups"], unit="MLUPS",
+                   h2d_bytes_per_step=e["h2d_per_step"], d2h_bytes_per_step=e["d2h_per_step"])
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, steps=1)
+    if rank == 0:
+        clocks = h["clocks"]
+        line = dict(
+            metric=METRIC, value=value, unit="MLUPS", n_gpus=world, steps=h["steps"],
+            warmup=args.warmup, ms_per_step=ms_max / h["steps"], higher_is_better=True,
+            scaling="weak", vs_baseline=None, dtype="f32" if head != "fp64" else "f64",
+            storage=head, data="synthetic",
+            config=dict(workload=WORKLOAD, shape=[256, 256, 256], lattice="D3Q27",
+                        collision="TRT 3/16", refill="eq", sigma=1e-4, gravity=1e-6,
+                        nu=round(inputs.DROP_NU, 9), parallelism=f"replicas{world}",
+                        l2="inputs larger than L2 (PDF buffers >= 1.8 GB)"),
+            roofline=by_prec[head]["roofline"], cpu_baseline=cpu, e2e=e2e,
+            gpu_launches=h["launches"],
+            clocks=dict(sm_mhz=clocks["sm_mhz"], sm_max_mhz=clocks["sm_max_mhz"],
+                        reasons=clocks["reasons"], samples=clocks["samples"]),
+            by_precision=by_prec,
+            speedup_vs_fp64=(h["mlups"] / res["fp64"]["mlups"]) if "fp64" in res else None,
+            speedup_vs_fp32=(h["mlups"] / res["fp32"]["mlups"]) if "fp32" in res else None,
+            stable=not unstable, unstable_steps=unstable or None,
+        )
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# FP64 operations per liquid-cell update of the stream-collide kernel for
+# D3Q27 TRT with Guo forcing (adds, multiplies, divides as written in the
+# kernel source, each shared subexpression counted once).
+FLOPS_PER_CELL_D3Q27_TRT = 1060
+# DRAM bytes per launch of k_stream_collide from the ncu capture summarised
+# under profiles/ (null until captured for the current kernel).
+TRAFFIC = {}
+
+if __name__ == "__main__":
+    main()

@@ -165,6 +165,18 @@ fsl_status fsl_lattice_table(int lattice, int* c3q, double* w);
 /* Number of kernel launches one fsl_step(1) issues. */
 int fsl_launches_per_step(const fsl_handle* h);
 
+/* Measurement of one kernel on the current state, for roofline reports.
+ * kernel: FSL_KERNEL_STREAM_COLLIDE, the bulk pull stream-collide pass over
+ * all cells (Eqs. nm-lbm-collision, nm-lbm-streaming; liquid cells).  Launches
+ * it `reps` times on the bound stream, each bracketed by CUDA events, and
+ * leaves the simulation state unchanged (the pass only reads the current PDF
+ * buffer and writes the other one).  out4 (host, 4 doubles): average launch
+ * time in ms, algorithmic bytes per launch (liquid cells x 2 q x storage bytes
+ * + one flag byte per cell + 4 bytes per interface cell listed), number of
+ * liquid cells, number of interface cells.  Synchronises the stream. */
+enum { FSL_KERNEL_STREAM_COLLIDE = 1 };
+fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4);
+
 /* Static description of a status code; last CUDA error text of this thread. */
 const char* fsl_status_string(fsl_status s);
 const char* fsl_last_error(void);

@@ -64,6 +64,7 @@ void make_geom(const fsl_config* c, Geom* g) {
   g->cells = (long long)g->sx * c->ny * c->nz;
   g->plane = (g->cells + 127) / 128 * 128;
   for (int a = 0; a < 3; ++a) g->periodic[a] = c->periodic[a] ? 1 : 0;
+  g->has_obst = 0;
 }
 
 void make_phys(const fsl_config* c, Phys* p) {
@@ -170,6 +171,19 @@ __global__ void __launch_bounds__(256) k_lost_partial(Dev d, Geom g, double* par
     if ((int)(c % g.sx) < g.nx) s += d.lost[c];
   const double b = block_sum<256>(s, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = b;
+}
+
+__global__ void k_count_types(Dev d, Geom g, unsigned long long* out) {
+  unsigned long long liq = 0, itf = 0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    if ((int)(c % g.sx) >= g.nx) continue;
+    const int t = d.flags[c] & F_TYPE;
+    liq += (t == T_LIQ);
+    itf += (t == T_IF);
+  }
+  atomicAdd(&out[0], liq);
+  atomicAdd(&out[1], itf);
 }
 
 __global__ void k_set_trace(Ctrl* ctrl, int every) {
@@ -291,6 +305,14 @@ fsl_status fsl_init_fill(fsl_handle* h, const double* phi, const double* u0,
     su = static_cast<double*>(h->d.pdf[1]);
     FSL_CK(cudaMemcpyAsync(su, u0, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
   }
+  // interior obstacles disable the obstacle-free fast paths; captured step
+  // graphs hold the geometry by value and are rebuilt
+  h->g.has_obst = 0;
+  if (obstacle)
+    for (size_t k = 0; k < n; ++k)
+      if (obstacle[k]) { h->g.has_obst = 1; break; }
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
   FSL_CK(h->L->init(h->d, h->g, h->p, 0, su, obstacle ? 1 : 0, h_ref, h->stream));
   k_set_trace<<<1, 32, 0, h->stream>>>(h->d.ctrl, h->trace_every);
   FSL_CK(cudaGetLastError());
@@ -507,6 +529,19 @@ fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
   std::vector<std::pair<char*, size_t>> parts;
   state_parts(h, c.step & 1, parts);
   const char* s = static_cast<const char*>(host_src);
+  // the flag bytes follow the PDF buffer: interior obstacles switch the
+  // obstacle-free fast paths off, and captured graphs hold the geometry
+  const unsigned char* fl = reinterpret_cast<const unsigned char*>(s + parts[0].second);
+  h->g.has_obst = 0;
+  for (int z = 0; z < h->g.nz && !h->g.has_obst; ++z)
+    for (int y = 0; y < h->g.ny && !h->g.has_obst; ++y)
+      for (int x = 0; x < h->g.nx; ++x)
+        if ((fl[x + (size_t)h->g.sx * (y + (size_t)h->g.ny * z)] & F_TYPE) == T_OBST) {
+          h->g.has_obst = 1;
+          break;
+        }
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
   for (auto& pr : parts) {
     FSL_CK(cudaMemcpyAsync(pr.first, s, pr.second, cudaMemcpyHostToDevice, h->stream));
     s += pr.second;
@@ -541,6 +576,46 @@ fsl_status fsl_lattice_table(int lattice, int* c3q, double* w) {
 }
 
 int fsl_launches_per_step(const fsl_handle* h) { return h ? h->L->launches_per_step : 0; }
+
+fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
+  if (!h || !out4 || reps < 1 || kernel != FSL_KERNEL_STREAM_COLLIDE) return FSL_ERR_ARG;
+  if (!h->ready) return FSL_ERR_STATE;
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(h->d.red + 2 * kReduceBlocks + 8);
+  FSL_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), h->stream));
+  k_count_types<<<kReduceBlocks, 256, 0, h->stream>>>(h->d, h->g, cnt);
+  FSL_CK(cudaGetLastError());
+  unsigned long long nc[2];
+  FSL_CK(cudaMemcpyAsync(nc, cnt, sizeof(nc), cudaMemcpyDeviceToHost, h->stream));
+  cudaEvent_t e0, e1;
+  FSL_CK(cudaEventCreate(&e0));
+  FSL_CK(cudaEventCreate(&e1));
+  double total_ms = 0.0;
+  cudaError_t err = cudaSuccess;
+  for (int r = 0; r < reps && err == cudaSuccess; ++r) {
+    err = cudaMemsetAsync(&h->d.ctrl->n_if, 0, sizeof(unsigned), h->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+    if (err == cudaSuccess) err = h->L->stream_collide(h->d, h->g, h->p, h->stream);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    total_ms += ms;
+  }
+  if (err == cudaSuccess) err = cudaMemsetAsync(&h->d.ctrl->n_if, 0, sizeof(unsigned), h->stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) return cuda_fail(err, "fsl_kernel_stats");
+  const double sb = (double)storage_bytes(h->cfg.precision);
+  const double cells = (double)h->g.nx * h->g.ny * h->g.nz;
+  out4[0] = total_ms / reps;
+  // liquid cells read and write q PDFs; every cell's flag byte is read; each
+  // interface cell index is appended to the interface list
+  out4[1] = (double)nc[0] * 2.0 * h->cfg.lattice * sb + cells * 1.0 + (double)nc[1] * 4.0;
+  out4[2] = (double)nc[0];
+  out4[3] = (double)nc[1];
+  return FSL_OK;
+}
 
 const char* fsl_status_string(fsl_status s) {
   switch (s) {

@@ -48,6 +48,7 @@ struct Geom {
   long long cells;     // padded cell count nz*ny*sx
   long long plane;     // PDF plane stride in elements (>= cells, 128-element multiple)
   int periodic[3];
+  int has_obst;        // the initial state had interior obstacle cells
 };
 
 struct Phys {
@@ -105,6 +106,8 @@ struct Launch {
   // decode plane i of pdf[cur] into dst (device, nx*ny*nz doubles, unpadded)
   cudaError_t (*export_pdf)(const Dev&, const Geom&, const Phys&, int cur, int i, double* dst,
                             cudaStream_t);
+  // the bulk stream-collide kernel alone (timing); leaves ctrl->n_if set
+  cudaError_t (*stream_collide)(const Dev&, const Geom&, const Phys&, cudaStream_t);
   int launches_per_step;
 };
 

@@ -30,6 +30,17 @@
 
 namespace fsl {
 
+#define FSL_GRID_LOOP(k, n) \
+  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < (n); k += gridDim.x * blockDim.x)
+// Warp-synchronous grid loop: all lanes of a warp run the same iterations
+// (k_ok says whether the lane's index is in range), so warp ballots may be
+// used inside to aggregate list appends.
+#define FSL_WARP_LOOP(k, k_ok, n)                                                             \
+  for (unsigned k##_base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31u; k##_base < (n);   \
+       k##_base += gridDim.x * blockDim.x)                                                    \
+    for (unsigned k = k##_base + (threadIdx.x & 31u), k##_once = 1; k##_once; k##_once = 0)  \
+      for (bool k_ok = k < (n), k##_o2 = true; k##_o2; k##_o2 = false)
+
 // ---------------------------------------------------------------- physics
 // Equilibrium (Eq. nm-lbm-equilibrium) in working representation.
 //   exact:   f_i^eq = w_i rho (1 + 3 cu + 4.5 cu^2 - 1.5 u.u)
@@ -57,13 +68,23 @@ __device__ __forceinline__ R guo_w(R ux, R uy, R uz, R Fx, R Fy, R Fz) {
 }
 
 // Zeroth moment (density) of working values, summed i = 0..Q-1.
+//   exact:   rho = f_0 + f_1 + ... + f_{Q-1}, left to right;
+//   shifted: drho = d_0 + (d_1 + d_2) + (d_3 + d_4) + ..., opposite pairs first
+//            (the order the pairwise collision of the 16/32-bit path uses).
 template <int Q, bool SHIFT, class R>
 __device__ __forceinline__ void density(const R* f, R& rho, R& drho) {
-  R s = (R)0;
+  R s = f[0];
+  if (SHIFT) {
 #pragma unroll
-  for (int i = 0; i < Q; ++i) s = (i == 0) ? f[0] : s + f[i];
-  if (SHIFT) { drho = s; rho = (R)1 + s; }
-  else { rho = s; drho = s - (R)1; }
+    for (int i = 1; i < Q; i += 2) s = s + (f[i] + f[i + 1]);
+    drho = s;
+    rho = (R)1 + s;
+  } else {
+#pragma unroll
+    for (int i = 1; i < Q; ++i) s = s + f[i];
+    rho = s;
+    drho = s - (R)1;
+  }
 }
 
 // First moment sum_i c_i f_i, summed in direction order with zero terms left out.
@@ -182,6 +203,184 @@ __device__ __forceinline__ void pull_liquid(const typename ST::T* __restrict__ A
   }
 }
 
+// ------------------------------------------------------------ 16/32-bit path
+// Collision of one cell in the even/odd (opposite-pair) form, FP32, values in
+// storage units (offsets f_i - w_i times S).  For a pair (i, i') = (i, opp i):
+//   f+ = (f_i + f_i')/2,  f- = (f_i - f_i')/2
+//   e+ = w (drho + rho (4.5 cu^2 - 1.5 u.u)),  e- = 3 w rho cu       (Eq. nm-lbm-equilibrium)
+//   G+ = w (9 cu cF - 3 u.F),                   G- = 3 w cF           (Eq. nm-lbm-force-guo)
+//   f*_i  = f_i  - [lam_e (f+ - e+) - pe G+] - [lam_o (f- - e-) - po G-]
+//   f*_i' = f_i' - [lam_e (f+ - e+) - pe G+] + [lam_o (f- - e-) - po G-]
+// which is the TRT update with Guo forcing; SRT is lam_o = lam_e = omega.
+template <int Q>
+__device__ __forceinline__ float collide_lp(const float* f, float* o, float lamE, float lamO,
+                                            float pe, float po, float gx, float gy, float gz,
+                                            float S, float& rho_out) {
+  constexpr int NP = (Q - 1) / 2;
+  float sp[NP], dp[NP];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    sp[k] = f[2 * k + 1] + f[2 * k + 2];
+    dp[k] = f[2 * k + 1] - f[2 * k + 2];
+  }
+  float acc = f[0];
+#pragma unroll
+  for (int k = 0; k < NP; ++k) acc = acc + sp[k];
+  const float drho = __fmul_rn(acc, 1.0f / S);
+  const float rho = 1.0f + drho;
+  float jx = 0.f, jy = 0.f, jz = 0.f;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int i = 2 * k + 1;
+    if (dir_c(i, 0) == 1) jx += dp[k]; else if (dir_c(i, 0) == -1) jx -= dp[k];
+    if (dir_c(i, 1) == 1) jy += dp[k]; else if (dir_c(i, 1) == -1) jy -= dp[k];
+    if (dir_c(i, 2) == 1) jz += dp[k]; else if (dir_c(i, 2) == -1) jz -= dp[k];
+  }
+  const float kk = (1.0f / S) / rho;
+  const float ux = fmaf(jx, kk, 0.5f * gx), uy = fmaf(jy, kk, 0.5f * gy), uz = fmaf(jz, kk, 0.5f * gz);
+  const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
+  const float usq = ux * ux + uy * uy + uz * uz;
+  const float uF = ux * Fx + uy * Fy + uz * Fz;
+  const float cst = drho - 1.5f * rho * usq;
+  // per weight class (index = |c|^2): constants in storage units
+  float A[4], Bc[4], O[4], GU[4], G9[4], G3[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float w = (float)wgt<Q>(c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 7 : (Q == 27 ? 19 : 7));
+    A[c] = (4.5f * w * S) * rho;
+    Bc[c] = (w * S) * cst;
+    O[c] = (3.0f * w * S) * rho;
+    GU[c] = (-3.0f * w * S * pe) * uF;
+    G9[c] = 9.0f * w * S * pe;
+    G3[c] = 3.0f * w * S * po;
+  }
+  o[0] = f[0] - fmaf(lamE, f[0] - Bc[0], -GU[0]);
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int i = 2 * k + 1;
+    const int c = len2(i);
+    const float cu = dot3r(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2), ux, uy, uz);
+    const float cF = dot3r(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2), Fx, Fy, Fz);
+    const float e = fmaf(A[c] * cu, cu, Bc[c]);
+    const float od = O[c] * cu;
+    const float Gp = fmaf(G9[c] * cu, cF, GU[c]);
+    const float Gm = G3[c] * cF;
+    const float Dp = fmaf(lamE, fmaf(0.5f, sp[k], -e), -Gp);
+    const float Dm = fmaf(lamO, fmaf(0.5f, dp[k], -od), -Gm);
+    o[i] = f[i] - Dp - Dm;
+    o[i + 1] = f[i + 1] - Dp + Dm;
+  }
+  rho_out = rho;
+  return usq;
+}
+
+// Bulk pass of the 16/32-bit path: two cells (x0, x0+1) per thread, pairs of
+// PDFs loaded as one aligned 4/8-byte word per direction; PDFs pulled from
+// x -/+ 1 come from the neighbouring lane by a warp shuffle (one extra
+// scalar load at the warp's edge or at a periodic wrap).  Liquid cells next
+// to a wall or obstacle take the per-direction bounce-back path.
+template <int Q, class ST>
+__global__ void __launch_bounds__(128) k_stream_collide_lp(Dev d, Geom g, Phys p) {
+  using T = typename ST::T;
+  constexpr float S = ST::kScaleF;
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int cur = ctrl->step & 1;
+  const T* __restrict__ A = (const T*)d.pdf[cur];
+  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
+  const long long P = g.plane;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int row = g.sx * (y + g.ny * z);
+  const bool in_row = x0 < g.sx;
+  const int xc = in_row ? x0 : g.sx - 2;  // clamped pair start for addressing
+  uint8_t fl0 = 0, fl1 = 0;
+  if (in_row) {
+    const uchar2 fl = *reinterpret_cast<const uchar2*>(d.flags + row + x0);
+    fl0 = x0 < g.nx ? fl.x : (uint8_t)T_GAS;
+    fl1 = x0 + 1 < g.nx ? fl.y : (uint8_t)T_GAS;
+  }
+  const int t0 = fl0 & F_TYPE, t1 = fl1 & F_TYPE;
+  warp_append(t0 == T_IF, row + x0, &ctrl->n_if, d.l_if);
+  warp_append(t1 == T_IF, row + x0 + 1, &ctrl->n_if, d.l_if);
+  const bool liq0 = t0 == T_LIQ, liq1 = t1 == T_LIQ;
+  if (!__any_sync(FULL, liq0 || liq1)) return;
+  // rows of the y/z neighbours (a wall side maps to the cell's own row: such
+  // cells are near-obstacle and never use the fast values)
+  int Yr[3], Zr[3];
+  Yr[1] = y; Zr[1] = z;
+  Yr[0] = y > 0 ? y - 1 : (g.periodic[1] ? g.ny - 1 : y);
+  Yr[2] = y < g.ny - 1 ? y + 1 : (g.periodic[1] ? 0 : y);
+  Zr[0] = z > 0 ? z - 1 : (g.periodic[2] ? g.nz - 1 : z);
+  Zr[2] = z < g.nz - 1 ? z + 1 : (g.periodic[2] ? 0 : z);
+  const int xm = x0 > 0 ? xc - 1 : (g.periodic[0] ? g.nx - 1 : 0);
+  const bool edge_hi = (lane == 31) || (x0 + 2 >= g.nx);
+  const int xp = (x0 + 2 < g.nx) ? x0 + 2 : ((g.periodic[0] && x0 + 2 == g.nx) ? 0 : xc);
+  float fa[Q], fb[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
+    const T* base = A + i * P + (long long)g.sx * (Yr[1 - cy] + g.ny * Zr[1 - cz]);
+    const float2 v = ST::ld2(base + xc);
+    if (cx == 0) {
+      fa[i] = v.x;
+      fb[i] = v.y;
+    } else if (cx == 1) {  // pulled from x - 1
+      const float up = __shfl_up_sync(FULL, v.y, 1);
+      fa[i] = (lane == 0) ? ST::ld1(base + xm) : up;
+      fb[i] = v.x;
+    } else {  // pulled from x + 1
+      const float dn = __shfl_down_sync(FULL, v.x, 1);
+      fa[i] = v.y;
+      fb[i] = edge_hi ? ST::ld1(base + xp) : dn;
+    }
+  }
+  const bool tr = p.trt != 0;
+  const float lamE = (float)p.lam_e, lamO = tr ? (float)p.lam_o : (float)p.omega;
+  const float pe = (float)p.pre_e, po = tr ? (float)p.pre_o : (float)p.pre_e;
+  const float gx = (float)p.g[0], gy = (float)p.g[1], gz = (float)p.g[2];
+  bool bad = false;
+  float o0[Q], o1[Q];
+  if (liq0) {
+    if (fl0 & F_NEAR_OBST) {
+      Nbr nb;
+      nb.setup(g, x0, y, z);
+      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0, true, fa);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fa[i] *= S;
+    }
+    float rho;
+    const float usq = collide_lp<Q>(fa, o0, lamE, lamO, pe, po, gx, gy, gz, S, rho);
+    bad |= !(usq < (float)(1.0 / 3.0));
+  }
+  if (liq1) {
+    if (fl1 & F_NEAR_OBST) {
+      Nbr nb;
+      nb.setup(g, x0 + 1, y, z);
+      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0 + 1, true, fb);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) fb[i] *= S;
+    }
+    float rho;
+    const float usq = collide_lp<Q>(fb, o1, lamE, lamO, pe, po, gx, gy, gz, S, rho);
+    bad |= !(usq < (float)(1.0 / 3.0));
+  }
+  T* out = B + row + x0;
+  if (liq0 && liq1) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st2(out + i * P, o0[i], o1[i]);
+  } else if (liq0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st1(out + i * P, o0[i]);
+  } else if (liq1) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st1(out + i * P + 1, o1[i]);
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
 // ------------------------------------------------------------ stream-collide
 // Pass over all cells: liquid cells stream and collide here; interface cells
 // are compacted (warp ballot) into l_if for k_stream_collide_if.
@@ -231,8 +430,10 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
   const long long P = g.plane;
   const unsigned nif = ctrl->n_if;
   bool bad = false;
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < nif; k += gridDim.x * blockDim.x) {
-    const int c = d.l_if[k];
+  FSL_WARP_LOOP(k, ok, nif) {
+    bool to_liq = false, to_gas = false;
+    const int c = ok ? d.l_if[k] : 0;
+    if (ok) {
     int x, y, z;
     cell_xyz(g, c, x, y, z);
     const uint8_t fl = d.flags[c];
@@ -265,11 +466,12 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
       else if (t == T_OBST) fin[i] = own[opp(i)];             /* halfway bounce-back */
       else fin[i] = feg[i] + feg[opp(i)] - own[opp(i)];       /* anti-bounce-back from gas */
     }
-    // Eq. nm-fslbm-mass-flux over i = 1..Q-1 (gas and walls carry none)
-    const double phx = d.phi[c];
+    // Eq. nm-fslbm-mass-flux over i = 1..Q-1 (gas and walls carry none), in
+    // the working precision (FP64 in the FP64 path)
+    const R phx = (R)d.phi[c];
     const int clsx = fl & (F_NF | F_NE);
     const bool thurey = !(p.options & 1u);
-    double dm = 0.0;
+    R dm = (R)0;
     bool dm_has = false;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
@@ -277,26 +479,26 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
       const int t = tn[io];  // the neighbour x + c_i sent f_io
       if (t != T_LIQ && t != T_IF) continue;
       // f_in = f*_io(x + c_i) = fin[io], f_out = f*_i(x) = own[i]
-      double dd;
-      const double both = (double)(fin[io] - own[i]);
+      R dd;
+      const R both = fin[io] - own[i];
       if (t == T_LIQ) {
         dd = both;
       } else {
         const int n = nb.at(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2));
         const int clsn = d.flags[n] & (F_NF | F_NE);
-        const double f_in = SH ? (double)fin[io] + wgt<Q>(io) : (double)fin[io];
-        const double f_out = SH ? (double)own[i] + wgt<Q>(i) : (double)own[i];
-        double br;
+        const R f_in = SH ? fin[io] + (R)wgt<Q>(io) : fin[io];
+        const R f_out = SH ? own[i] + (R)wgt<Q>(i) : own[i];
+        R br;
         if (!thurey) br = both;
         else if (clsx == 0) br = (clsn == F_NF) ? f_in : (clsn == F_NE) ? -f_out : both;
         else if (clsx == F_NF) br = (clsn == F_NF) ? both : -f_out;
         else br = (clsn == F_NE) ? both : f_in;
-        dd = 0.5 * (phx + d.phi[n]) * br;
+        dd = (R)0.5 * (phx + (R)d.phi[n]) * br;
       }
       dm = dm_has ? dm + dd : dd;
       dm_has = true;
     }
-    const double m_new = dm_has ? d.mass[c] + dm : d.mass[c];
+    const double m_new = dm_has ? d.mass[c] + (double)dm : d.mass[c];
     R fout[Q], rho;
     const R usq = collide<Q, SH, R>(fin, fout, p, rho);
     if (!(usq < (R)(1.0 / 3.0))) bad = true;
@@ -309,46 +511,52 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
     d.phinew[c] = ph;
     if (ph > p.thr_hi) {
       d.flags[c] = fl | F_TO_LIQ;
-      d.l_fill[atomicAdd(&ctrl->n_fill, 1u)] = c;
+      to_liq = true;
     } else if (ph < p.thr_lo) {
       d.flags[c] = fl | F_TO_GAS;
-      d.l_empty[atomicAdd(&ctrl->n_empty, 1u)] = c;
+      to_gas = true;
     }
+    }
+    warp_append(to_liq, c, &ctrl->n_fill, d.l_fill);
+    warp_append(to_gas, c, &ctrl->n_empty, d.l_empty);
   }
   if (bad) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
 }
 
 // ------------------------------------------------------------ conversion
-#define FSL_GRID_LOOP(k, n) \
-  for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < (n); k += gridDim.x * blockDim.x)
+
 
 template <int Q>
 __global__ void __launch_bounds__(256) k_fill(Dev d, Geom g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nif = ctrl->n_if, nfill = ctrl->n_fill;
-  FSL_GRID_LOOP(k, nif + nfill) {
-    if (k < nif) {
+  FSL_WARP_LOOP(k, ok, nif + nfill) {
+    if (ok && k < nif) {
       const int c = d.l_if[k];
       d.phi[c] = d.phinew[c];
-      continue;
     }
-    const int c = d.l_fill[k - nif];
-    int x, y, z;
-    cell_xyz(g, c, x, y, z);
+    const bool filling = ok && k >= nif;
+    int x = 0, y = 0, z = 0;
+    if (filling) cell_xyz(g, d.l_fill[k - nif], x, y, z);
     for (int i = 1; i < Q; ++i) {
-      const int n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-      if (n < 0) continue;
-      if ((d.flags[n] & F_TYPE) == T_GAS) {
-        uint8_t old = byte_or(d.flags, n, (uint8_t)(F_NEW | T_IF));
-        if (!(old & F_NEW)) {
-          d.phi[n] = 0.0;
-          d.mass[n] = 0.0;
-          unsigned slot = atomicAdd(&ctrl->n_new, 1u);
-          d.l_new[slot] = n;
+      int n = -1;
+      bool created = false;
+      if (filling) {
+        n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
+        if (n >= 0) {
+          if ((d.flags[n] & F_TYPE) == T_GAS) {
+            const uint8_t old = byte_or(d.flags, n, (uint8_t)(F_NEW | T_IF));
+            if (!(old & F_NEW)) {
+              d.phi[n] = 0.0;
+              d.mass[n] = 0.0;
+              created = true;
+            }
+          }
+          if (d.flags[n] & F_TO_GAS) byte_and(d.flags, n, F_TO_GAS);
         }
       }
-      if (d.flags[n] & F_TO_GAS) byte_and(d.flags, n, F_TO_GAS);
+      warp_append(created, n, &ctrl->n_new, d.l_new);
     }
   }
 }
@@ -362,30 +570,34 @@ __global__ void __launch_bounds__(256) k_empty(Dev d, Geom g) {
   const int cur = ctrl->step & 1;
   const typename ST::T* A = (const typename ST::T*)d.pdf[cur];
   const unsigned ne = ctrl->n_empty;
-  FSL_GRID_LOOP(k, ne) {
-    const int c = d.l_empty[k];
-    if (!(d.flags[c] & F_TO_GAS)) continue;
-    int x, y, z;
-    cell_xyz(g, c, x, y, z);
+  FSL_WARP_LOOP(k, ok, ne) {
+    const int c = ok ? d.l_empty[k] : 0;
+    const bool emptying = ok && (d.flags[c] & F_TO_GAS);
+    int x = 0, y = 0, z = 0;
+    if (emptying) cell_xyz(g, c, x, y, z);
     for (int i = 1; i < Q; ++i) {
-      const int n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-      if (n < 0) continue;
-      if ((d.flags[n] & F_TYPE) != T_LIQ) continue;
-      if (!byte_retype(d.flags, n, T_LIQ, T_IF, &ctrl->timeout)) continue;
-      // the liquid cell's density of this step, recomputed exactly as the
-      // stream-collide pass obtained it
-      int nx_, ny_, nz_;
-      cell_xyz(g, n, nx_, ny_, nz_);
-      Nbr nb;
-      nb.setup(g, nx_, ny_, nz_);
-      R fin[Q], rho, drho;
-      pull_liquid<Q, ST>(A, g.plane, d.flags, nb, n, (d.flags[n] & F_NEAR_OBST) != 0, fin);
-      density<Q, SH, R>(fin, rho, drho);
-      d.rho[n] = (double)rho;
-      d.mass[n] = (double)rho;
-      d.phi[n] = 1.0;
-      unsigned slot = atomicAdd(&ctrl->n_l2i, 1u);
-      d.l_l2i[slot] = n;
+      int n = -1;
+      bool won = false;
+      if (emptying) {
+        n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
+        if (n >= 0 && (d.flags[n] & F_TYPE) == T_LIQ &&
+            byte_retype(d.flags, n, T_LIQ, T_IF, &ctrl->timeout)) {
+          // the liquid cell's density of this step, recomputed exactly as the
+          // stream-collide pass obtained it
+          int nx_, ny_, nz_;
+          cell_xyz(g, n, nx_, ny_, nz_);
+          Nbr nb;
+          nb.setup(g, nx_, ny_, nz_);
+          R fin[Q], rho, drho;
+          pull_liquid<Q, ST>(A, g.plane, d.flags, nb, n, (d.flags[n] & F_NEAR_OBST) != 0, fin);
+          density<Q, SH, R>(fin, rho, drho);
+          d.rho[n] = (double)rho;
+          d.mass[n] = (double)rho;
+          d.phi[n] = 1.0;
+          won = true;
+        }
+      }
+      warp_append(won, n, &ctrl->n_l2i, d.l_l2i);
     }
   }
 }
@@ -418,60 +630,58 @@ static __global__ void __launch_bounds__(256) k_finalise(Dev d) {
 // difference across the 3x3 block perpendicular to a with weights 4 (centre),
 // 2 (edges), 1 (corners), divided by 32; exact for linear phi.  An axis whose
 // block touches a wall or obstacle uses a two-point difference over the
-// non-obstacle cells instead (narrowed stencil near obstacles).
+// non-obstacle cells instead (narrowed stencil near obstacles).  RC is the
+// compute type: FP64 in the FP64 path, FP32 otherwise.
+template <class RC>
 __device__ inline void normal_py(const Geom& g, const uint8_t* flags, const double* phi, int x,
-                                 int y, int z, double* n) {
+                                 int y, int z, RC* n) {
   const int p[3] = {x, y, z};
   const int c = x + g.sx * (y + g.ny * z);
   for (int a = 0; a < 3; ++a) {
     int b = (a + 1) % 3, cc = (a + 2) % 3;
     if (b > cc) { int t = b; b = cc; cc = t; }
+    int yp_[9], ym_[9];
     bool touches = false;
-    for (int ob = -1; ob <= 1 && !touches; ++ob)
-      for (int oc = -1; oc <= 1 && !touches; ++oc) {
+    for (int ob = -1; ob <= 1; ++ob)
+      for (int oc = -1; oc <= 1; ++oc) {
         int dp[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
         dp[a] = 1; dm[a] = -1;
         dp[b] += ob; dm[b] += ob;
         dp[cc] += oc; dm[cc] += oc;
-        int yp = nb_at(g, p[0], p[1], p[2], dp[0], dp[1], dp[2]);
-        int ym = nb_at(g, p[0], p[1], p[2], dm[0], dm[1], dm[2]);
-        if (type_at(flags, yp) == T_OBST || type_at(flags, ym) == T_OBST) touches = true;
+        const int k = 3 * (ob + 1) + (oc + 1);
+        yp_[k] = nb_at(g, p[0], p[1], p[2], dp[0], dp[1], dp[2]);
+        ym_[k] = nb_at(g, p[0], p[1], p[2], dm[0], dm[1], dm[2]);
+        if (type_at(flags, yp_[k]) == T_OBST || type_at(flags, ym_[k]) == T_OBST) touches = true;
       }
     if (!touches) {
-      double sum = 0.0;
+      RC sum = (RC)0;
       for (int ob = -1; ob <= 1; ++ob)
         for (int oc = -1; oc <= 1; ++oc) {
-          int dp[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
-          dp[a] = 1; dm[a] = -1;
-          dp[b] += ob; dm[b] += ob;
-          dp[cc] += oc; dm[cc] += oc;
-          int yp = nb_at(g, p[0], p[1], p[2], dp[0], dp[1], dp[2]);
-          int ym = nb_at(g, p[0], p[1], p[2], dm[0], dm[1], dm[2]);
-          double w = (ob == 0 ? 2.0 : 1.0) * (oc == 0 ? 2.0 : 1.0);
-          sum += w * (phi[yp] - phi[ym]);
+          const int k = 3 * (ob + 1) + (oc + 1);
+          const RC w = (RC)((ob == 0 ? 2.0 : 1.0) * (oc == 0 ? 2.0 : 1.0));
+          const RC t = w * ((RC)phi[yp_[k]] - (RC)phi[ym_[k]]);
+          sum = (k == 0) ? (RC)0 + t : sum + t;
         }
-      n[a] = sum / 32.0;
+      n[a] = sum / (RC)32;
     } else {
-      int dp[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
-      dp[a] = 1; dm[a] = -1;
-      int yp = nb_at(g, p[0], p[1], p[2], dp[0], dp[1], dp[2]);
-      int ym = nb_at(g, p[0], p[1], p[2], dm[0], dm[1], dm[2]);
-      bool okp = type_at(flags, yp) != T_OBST, okm = type_at(flags, ym) != T_OBST;
-      if (okp && okm) n[a] = 0.5 * (phi[yp] - phi[ym]);
-      else if (okp) n[a] = phi[yp] - phi[c];
-      else if (okm) n[a] = phi[c] - phi[ym];
-      else n[a] = 0.0;
+      const int yp = yp_[4], ym = ym_[4];
+      const bool okp = type_at(flags, yp) != T_OBST, okm = type_at(flags, ym) != T_OBST;
+      if (okp && okm) n[a] = (RC)0.5 * ((RC)phi[yp] - (RC)phi[ym]);
+      else if (okp) n[a] = (RC)phi[yp] - (RC)phi[c];
+      else if (okm) n[a] = (RC)phi[c] - (RC)phi[ym];
+      else n[a] = (RC)0;
     }
   }
 }
 
+template <class RC>
 __device__ inline void unit_normal(const Geom& g, const uint8_t* flags, const double* phi, int x,
-                                   int y, int z, double* nh) {
-  double n[3];
-  normal_py(g, flags, phi, x, y, z, n);
-  double len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-  if (len < 1e-12) {
-    nh[0] = nh[1] = nh[2] = 0.0;
+                                   int y, int z, RC* nh) {
+  RC n[3];
+  normal_py<RC>(g, flags, phi, x, y, z, n);
+  const RC len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  if (len < (RC)1e-12) {
+    nh[0] = nh[1] = nh[2] = (RC)0;
   } else {
     nh[0] = n[0] / len;
     nh[1] = n[1] / len;
@@ -479,47 +689,131 @@ __device__ inline void unit_normal(const Geom& g, const uint8_t* flags, const do
   }
 }
 
+// coordinate v wrapped into [0, n) (periodic axes; v within one period)
+__device__ __forceinline__ int wrapc(int v, int n) {
+  if (v < 0) v += n;
+  else if (v >= n) v -= n;
+  return (v < 0 || v >= n) ? ((v % n) + n) % n : v;
+}
+
 // K = -div(n_hat), central differences over the face neighbours; a wall side
 // is replaced by the centre value.
-__device__ inline double curvature(const Geom& g, const uint8_t* flags, const double* phi, int x,
-                                   int y, int z) {
-  double nc[3];
-  unit_normal(g, flags, phi, x, y, z, nc);
-  double div = 0.0;
+template <class RC>
+__device__ inline RC curvature(const Geom& g, const uint8_t* flags, const double* phi, int x,
+                               int y, int z) {
+  RC nc[3];
+  unit_normal<RC>(g, flags, phi, x, y, z, nc);
+  RC div = (RC)0;
   for (int a = 0; a < 3; ++a) {
     int dp[3] = {0, 0, 0}, dm[3] = {0, 0, 0};
     dp[a] = 1; dm[a] = -1;
-    int yp = nb_at(g, x, y, z, dp[0], dp[1], dp[2]);
-    int ym = nb_at(g, x, y, z, dm[0], dm[1], dm[2]);
-    bool okp = type_at(flags, yp) != T_OBST, okm = type_at(flags, ym) != T_OBST;
-    double np[3], nm[3], dd;
+    const int yp = nb_at(g, x, y, z, dp[0], dp[1], dp[2]);
+    const int ym = nb_at(g, x, y, z, dm[0], dm[1], dm[2]);
+    const bool okp = type_at(flags, yp) != T_OBST, okm = type_at(flags, ym) != T_OBST;
+    RC np[3], nm[3], dd;
+    const int px = wrapc(x + dp[0], g.nx), py = wrapc(y + dp[1], g.ny), pz = wrapc(z + dp[2], g.nz);
+    const int mx = wrapc(x + dm[0], g.nx), my = wrapc(y + dm[1], g.ny), mz = wrapc(z + dm[2], g.nz);
     if (okp && okm) {
-      int px, py, pz, mx, my, mz;
-      cell_xyz(g, yp, px, py, pz);
-      cell_xyz(g, ym, mx, my, mz);
-      unit_normal(g, flags, phi, px, py, pz, np);
-      unit_normal(g, flags, phi, mx, my, mz, nm);
-      dd = 0.5 * (np[a] - nm[a]);
+      unit_normal<RC>(g, flags, phi, px, py, pz, np);
+      unit_normal<RC>(g, flags, phi, mx, my, mz, nm);
+      dd = (RC)0.5 * (np[a] - nm[a]);
     } else if (okp) {
-      int px, py, pz;
-      cell_xyz(g, yp, px, py, pz);
-      unit_normal(g, flags, phi, px, py, pz, np);
+      unit_normal<RC>(g, flags, phi, px, py, pz, np);
       dd = np[a] - nc[a];
     } else if (okm) {
-      int mx, my, mz;
-      cell_xyz(g, ym, mx, my, mz);
-      unit_normal(g, flags, phi, mx, my, mz, nm);
+      unit_normal<RC>(g, flags, phi, mx, my, mz, nm);
       dd = nc[a] - nm[a];
     } else {
-      dd = 0.0;
+      dd = (RC)0;
     }
-    div += dd;
+    div = (a == 0) ? (RC)0 + dd : div + dd;
   }
   return -div;
 }
 
+// The same curvature for a cell whose distance-2 neighbourhood holds no wall
+// or obstacle: no type checks, wrapped coordinates computed once.  Same
+// operation order as curvature(), so the results are identical.
+template <class RC>
+__device__ inline RC curvature_open(const Geom& g, const double* phi, int x, int y, int z) {
+  int X[5], Y[5], Z[5];
+#pragma unroll
+  for (int o = 0; o < 5; ++o) {
+    X[o] = wrapc(x + o - 2, g.nx);
+    Y[o] = wrapc(y + o - 2, g.ny);
+    Z[o] = wrapc(z + o - 2, g.nz);
+  }
+  RC div = (RC)0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    RC nh[2][3];
+#pragma unroll
+    for (int sgn = 0; sgn < 2; ++sgn) {
+      // point p = centre + (+1 | -1) e_a, in offset coordinates (2 = centre)
+      int pc[3] = {2, 2, 2};
+      pc[a] += sgn == 0 ? 1 : -1;
+      RC v[3][3][3];  // phi around p, v[dz+1][dy+1][dx+1]
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz)
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+          for (int dx = -1; dx <= 1; ++dx)
+            v[dz + 1][dy + 1][dx + 1] =
+                (RC)phi[X[pc[0] + dx] + g.sx * (Y[pc[1] + dy] + g.ny * Z[pc[2] + dz])];
+      RC n[3];
+#pragma unroll
+      for (int ax = 0; ax < 3; ++ax) {
+        int b = (ax + 1) % 3, cc = (ax + 2) % 3;
+        if (b > cc) { int t = b; b = cc; cc = t; }
+        RC sum = (RC)0;
+#pragma unroll
+        for (int ob = -1; ob <= 1; ++ob)
+#pragma unroll
+          for (int oc = -1; oc <= 1; ++oc) {
+            int op[3] = {0, 0, 0}, om[3] = {0, 0, 0};
+            op[ax] = 1; om[ax] = -1;
+            op[b] += ob; om[b] += ob;
+            op[cc] += oc; om[cc] += oc;
+            const RC w = (RC)((ob == 0 ? 2.0 : 1.0) * (oc == 0 ? 2.0 : 1.0));
+            const RC t = w * (v[op[2] + 1][op[1] + 1][op[0] + 1] - v[om[2] + 1][om[1] + 1][om[0] + 1]);
+            sum = (ob == -1 && oc == -1) ? (RC)0 + t : sum + t;
+          }
+        n[ax] = sum / (RC)32;
+      }
+      const RC len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      if (len < (RC)1e-12) {
+        nh[sgn][0] = nh[sgn][1] = nh[sgn][2] = (RC)0;
+      } else {
+        nh[sgn][0] = n[0] / len;
+        nh[sgn][1] = n[1] / len;
+        nh[sgn][2] = n[2] / len;
+      }
+    }
+    const RC dd = (RC)0.5 * (nh[0][a] - nh[1][a]);
+    div = (a == 0) ? (RC)0 + dd : div + dd;
+  }
+  return -div;
+}
+
+// true when no cell within distance 2 of (x, y, z) can be a wall or obstacle
+__device__ __forceinline__ bool open_neighbourhood(const Geom& g, int x, int y, int z) {
+  if (g.has_obst) return false;
+  if (!g.periodic[0] && (x < 2 || x > g.nx - 3)) return false;
+  if (!g.periodic[1] && (y < 2 || y > g.ny - 3)) return false;
+  if (!g.periodic[2] && (z < 2 || z > g.nz - 3)) return false;
+  return true;
+}
+
+template <class RC>
+__device__ inline RC curvature_any(const Geom& g, const uint8_t* flags, const double* phi, int x,
+                                   int y, int z) {
+  return open_neighbourhood(g, x, y, z) ? curvature_open<RC>(g, phi, x, y, z)
+                                        : curvature<RC>(g, flags, phi, x, y, z);
+}
+
 // ------------------------------------------------------------ refilling
-// plain FP64 equilibrium for a runtime direction (list kernels, initial state)
+// plain FP64 equilibrium for a runtime direction (initial state)
 template <int Q>
 __device__ inline double feq_d(int i, double rho, double ux, double uy, double uz) {
   const double cu = (double)rc(i, 0) * ux + (double)rc(i, 1) * uy + (double)rc(i, 2) * uz;
@@ -527,8 +821,19 @@ __device__ inline double feq_d(int i, double rho, double ux, double uy, double u
   return rw<Q>(i) * rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * usq);
 }
 
-// stored moments of cell n from full PDFs (double): rho = sum f*,
-// u = sum c f* / rho - g / 2
+// equilibrium of a runtime direction in working representation (Eq.
+// nm-lbm-equilibrium): f_i^eq, or f_i^eq - w_i in the shifted representation
+template <int Q, bool SHIFT, class R>
+__device__ inline R feq_rt(int i, R rho, R drho, R ux, R uy, R uz) {
+  const R cu = (R)rc(i, 0) * ux + (R)rc(i, 1) * uy + (R)rc(i, 2) * uz;
+  const R usq = ux * ux + uy * uy + uz * uz;
+  const R w = (R)rw<Q>(i);
+  if (!SHIFT) return w * rho * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * usq);
+  return w * (drho + rho * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * usq));
+}
+
+// stored moments of cell n (double, full PDFs): rho = sum f*,
+// u = sum c f* / rho - g / 2  (observation kernels)
 template <int Q, class ST>
 __device__ inline void stored_moments(const typename ST::T* B, long long plane, int n,
                                       const Phys& p, double& rho, double* u) {
@@ -545,138 +850,179 @@ __device__ inline void stored_moments(const typename ST::T* B, long long plane, 
   u[2] = jz / r - 0.5 * p.g[2];
 }
 
+// the same in working representation and precision
+template <int Q, class ST>
+__device__ inline void stored_moments_w(const typename ST::T* B, long long plane, int n,
+                                        const Phys& p, typename ST::R& rho,
+                                        typename ST::R& drho, typename ST::R* u) {
+  using R = typename ST::R;
+  R f[Q], jx, jy, jz;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) f[i] = ST::ldw(B + i * plane + n);
+  density<Q, ST::kShift, R>(f, rho, drho);
+  momentum<Q, R>(f, jx, jy, jz);
+  u[0] = jx / rho - (R)0.5 * (R)p.g[0];
+  u[1] = jy / rho - (R)0.5 * (R)p.g[1];
+  u[2] = jz / rho - (R)0.5 * (R)p.g[2];
+}
+
 __device__ __forceinline__ bool valid_src(const uint8_t* flags, int n) {
   if (n < 0) return false;
   const uint8_t f = flags[n];
   return is_fluid(f & F_TYPE) && !(f & F_NEW);
 }
 
+// Refilling (Sec. 3.1), one warp per new interface cell: lane i examines the
+// neighbour x + c_i and writes the refilled f_i; sums over the valid
+// neighbours run in direction order (shuffled to every lane), so the FP64
+// result equals a sequential evaluation in that order.
 template <int Q, class ST>
 __global__ void __launch_bounds__(128) k_refill(Dev d, Geom g, Phys p) {
   using T = typename ST::T;
+  using R = typename ST::R;
+  constexpr bool SH = ST::kShift;
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const int cur = ctrl->step & 1;
   T* B = (T*)d.pdf[cur ^ 1];
   const long long P = g.plane;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
   const unsigned nn = ctrl->n_new;
-  FSL_GRID_LOOP(k, nn) {
+  const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
+  const int scheme = p.refill;
+  for (unsigned k = wid; k < nn; k += nw) {
     const int c = d.l_new[k];
     int x, y, z;
     cell_xyz(g, c, x, y, z);
-    bool valid[Q];
-    int nbr[Q];
-    double nrho[Q], nux[Q], nuy[Q], nuz[Q];
-    int count = 0;
-    double rsum = 0.0, usx = 0.0, usy = 0.0, usz = 0.0;
-    valid[0] = false;
-    nbr[0] = c;
-    for (int i = 1; i < Q; ++i) {
-      const int n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-      nbr[i] = n;
-      valid[i] = valid_src(d.flags, n);
-      if (valid[i]) {
-        double u[3];
-        stored_moments<Q, ST>(B, P, n, p, nrho[i], u);
-        nux[i] = u[0]; nuy[i] = u[1]; nuz[i] = u[2];
-        rsum += nrho[i];
-        usx += nux[i]; usy += nuy[i]; usz += nuz[i];
-        count += 1;
+    int n = -1;
+    bool valid = false;
+    R nr = (R)0, ndr = (R)0, nu[3] = {(R)0, (R)0, (R)0};
+    if (lane >= 1 && lane < Q) {
+      n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
+      valid = valid_src(d.flags, n);
+      if (valid) stored_moments_w<Q, ST>(B, P, n, p, nr, ndr, nu);
+    }
+    const unsigned vmask = __ballot_sync(FULL, valid);
+    const int count = __popc(vmask);
+    // rho_bar, u_bar: plain means over the valid neighbours (R7)
+    R rsum = (R)0, dsum = (R)0, sx = (R)0, sy = (R)0, sz = (R)0;
+    for (int j = 1; j < Q; ++j) {
+      const R a = __shfl_sync(FULL, nr, j), b = __shfl_sync(FULL, ndr, j);
+      const R vx = __shfl_sync(FULL, nu[0], j), vy = __shfl_sync(FULL, nu[1], j),
+              vz = __shfl_sync(FULL, nu[2], j);
+      if ((vmask >> j) & 1u) {
+        rsum = rsum + a;
+        dsum = dsum + b;
+        sx = sx + vx;
+        sy = sy + vy;
+        sz = sz + vz;
       }
     }
-    double out[Q];
-    const double cnt = (double)(count > 0 ? count : 1);
-    const double rb = rsum / cnt, ubx = usx / cnt, uby = usy / cnt, ubz = usz / cnt;
-    const int scheme = p.refill;
+    const R cnt = (R)(count > 0 ? count : 1);
+    const R rb = rsum / cnt, drb = dsum / cnt;
+    const R ubx = sx / cnt, uby = sy / cnt, ubz = sz / cnt;
+    // direction best aligned with the interface normal among valid ones
     int dn = -1;
     if (scheme == 1 || scheme == 3) {
-      double n3[3];
-      normal_py(g, d.flags, d.phi, x, y, z, n3);
-      double best = 0.0;
-      for (int i = 1; i < Q; ++i) {
-        if (!valid[i]) continue;
-        const double dot = (double)rc(i, 0) * n3[0] + (double)rc(i, 1) * n3[1] +
-                           (double)rc(i, 2) * n3[2];
-        if (dn < 0 || dot > best) { dn = i; best = dot; }
+      R n3[3];
+      normal_py<R>(g, d.flags, d.phi, x, y, z, n3);
+      R best = (R)0;
+      for (int j = 1; j < Q; ++j) {
+        if (!((vmask >> j) & 1u)) continue;
+        const R dot = (R)rc(j, 0) * n3[0] + (R)rc(j, 1) * n3[1] + (R)rc(j, 2) * n3[2];
+        if (dn < 0 || dot > best) { dn = j; best = dot; }
       }
     }
-    if (count == 0 || ((scheme == 1 || scheme == 3) && dn < 0)) {
+    const int i = lane;
+    R out = (R)0;
+    const bool bad = count == 0 || ((scheme == 1 || scheme == 3) && dn < 0);
+    if (bad) {
       // unreachable for cells created by a filling neighbour; latch the event
-      atomicOr(&ctrl->timeout, 2u);
-      for (int i = 0; i < Q; ++i) out[i] = rw<Q>(i);
-    } else if (scheme == 0) {  // EQ
-      for (int i = 0; i < Q; ++i) out[i] = feq_d<Q>(i, rb, ubx, uby, ubz);
-    } else if (scheme == 1) {  // EQ+NEQ
-      const int yn = nbr[dn];
-      for (int i = 0; i < Q; ++i) {
-        const double fe = feq_d<Q>(i, rb, ubx, uby, ubz);
-        const double fy = ST::ldf(B + i * P + yn, rw<Q>(i));
-        double fneq;
-        if (p.options & 4u) fneq = fy - fe;
-        else fneq = fy - feq_d<Q>(i, nrho[dn], nux[dn], nuy[dn], nuz[dn]);
-        out[i] = fe + fneq;
-      }
-    } else if (scheme == 2) {  // GEQ
-      double du[3][3];
-      const double ub[3] = {ubx, uby, ubz};
-      for (int b = 0; b < 3; ++b) {
-        const int dp = 1 + 2 * b, dm = 2 + 2 * b;
-        for (int a = 0; a < 3; ++a) {
-          const double up = a == 0 ? nux[dp] : a == 1 ? nuy[dp] : nuz[dp];
-          const double um = a == 0 ? nux[dm] : a == 1 ? nuy[dm] : nuz[dm];
-          if (valid[dp] && valid[dm]) du[a][b] = 0.5 * (up - um);
-          else if (valid[dp]) du[a][b] = up - ub[a];
-          else if (valid[dm]) du[a][b] = ub[a] - um;
-          else du[a][b] = 0.0;
+      if (lane == 0) atomicOr(&ctrl->timeout, 2u);
+      out = SH ? (R)0 : (R)(i < Q ? rw<Q>(i) : 0.0);
+    } else if (scheme == 0 || scheme == 1 || scheme == 2) {
+      const int li = i < Q ? i : 0;
+      const R fe = feq_rt<Q, SH, R>(li, rb, drb, ubx, uby, ubz);
+      out = fe;
+      if (scheme == 1) {  // EQ+NEQ (R8: the neighbour's own equilibrium)
+        const int yn = __shfl_sync(FULL, n, dn);
+        const R ry = __shfl_sync(FULL, nr, dn), dry = __shfl_sync(FULL, ndr, dn);
+        const R vx = __shfl_sync(FULL, nu[0], dn), vy = __shfl_sync(FULL, nu[1], dn),
+                vz = __shfl_sync(FULL, nu[2], dn);
+        if (i < Q) {
+          const R fy = ST::ldw(B + i * P + yn);
+          R fneq;
+          if (p.options & 4u) fneq = fy - fe;
+          else fneq = fy - feq_rt<Q, SH, R>(i, ry, dry, vx, vy, vz);
+          out = fe + fneq;
         }
-      }
-      const double coef = p.geq_coef;
-      for (int i = 0; i < Q; ++i) {
-        const int cc[3] = {rc(i, 0), rc(i, 1), rc(i, 2)};
-        double sum = 0.0;
+      } else if (scheme == 2) {  // GEQ (R9: prefactor 1/(2 c_s^2 omega))
+        R vel[7][3];
+        for (int j = 1; j <= 6; ++j) {
+          vel[j][0] = __shfl_sync(FULL, nu[0], j);
+          vel[j][1] = __shfl_sync(FULL, nu[1], j);
+          vel[j][2] = __shfl_sync(FULL, nu[2], j);
+        }
+        const R ub[3] = {ubx, uby, ubz};
+        R du[3][3];
+        for (int b = 0; b < 3; ++b) {
+          const int dp = 1 + 2 * b, dm = 2 + 2 * b;
+          const bool vp = (vmask >> dp) & 1u, vm = (vmask >> dm) & 1u;
+          for (int a = 0; a < 3; ++a) {
+            if (vp && vm) du[a][b] = (R)0.5 * (vel[dp][a] - vel[dm][a]);
+            else if (vp) du[a][b] = vel[dp][a] - ub[a];
+            else if (vm) du[a][b] = ub[a] - vel[dm][a];
+            else du[a][b] = (R)0;
+          }
+        }
+        const R coef = (R)p.geq_coef;
+        const int cc[3] = {rc(li, 0), rc(li, 1), rc(li, 2)};
+        R sum = (R)0;
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b) {
-            const double S = du[a][b] + du[b][a];
-            const double Qab = (a == b ? 1.0 / 3.0 : 0.0) - (double)(cc[a] * cc[b]);
-            sum += S * Qab;
+            const R Sab = du[a][b] + du[b][a];
+            const R Qab = (a == b ? (R)(1.0 / 3.0) : (R)0) - (R)(cc[a] * cc[b]);
+            sum = sum + Sab * Qab;
           }
-        out[i] = feq_d<Q>(i, rb, ubx, uby, ubz) + rw<Q>(i) * rb * coef * sum;
+        out = fe + (R)rw<Q>(li) * rb * coef * sum;
       }
-    } else if (scheme == 3) {  // EXT
+    } else if (scheme == 3) {  // EXT, second order with lower-order fallbacks
       const int cx = rc(dn, 0), cy = rc(dn, 1), cz = rc(dn, 2);
-      const int y1 = nbr[dn];
+      const int y1 = __shfl_sync(FULL, n, dn);
       const int y2 = nb_at(g, x, y, z, 2 * cx, 2 * cy, 2 * cz);
       const int y3 = nb_at(g, x, y, z, 3 * cx, 3 * cy, 3 * cz);
       int kk = 1;
       const bool v2 = valid_src(d.flags, y2), v3 = valid_src(d.flags, y3);
       if (v2) kk = v3 ? 3 : 2;
-      for (int i = 0; i < Q; ++i) {
-        const double w = rw<Q>(i);
-        const double f1 = ST::ldf(B + i * P + y1, w);
+      if (i < Q) {
+        const R f1 = ST::ldw(B + i * P + y1);
         if (kk == 3) {
-          const double f2 = ST::ldf(B + i * P + y2, w), f3 = ST::ldf(B + i * P + y3, w);
-          out[i] = 3.0 * f1 - 3.0 * f2 + f3;
+          const R f2 = ST::ldw(B + i * P + y2), f3 = ST::ldw(B + i * P + y3);
+          out = (R)3 * f1 - (R)3 * f2 + f3;
         } else if (kk == 2) {
-          const double f2 = ST::ldf(B + i * P + y2, w);
-          out[i] = 2.0 * f1 - f2;
+          out = (R)2 * f1 - ST::ldw(B + i * P + y2);
         } else {
-          out[i] = f1;
+          out = f1;
         }
       }
     } else {  // AVG
-      for (int i = 0; i < Q; ++i) {
-        double sum = 0.0;
-        for (int j = 1; j < Q; ++j)
-          if (valid[j]) sum += ST::ldf(B + i * P + nbr[j], rw<Q>(i));
-        out[i] = sum / cnt;
+      R sum = (R)0;
+      for (int j = 1; j < Q; ++j) {
+        const int nj = __shfl_sync(FULL, n, j);
+        if (((vmask >> j) & 1u) && i < Q) sum = sum + ST::ldw(B + i * P + nj);
       }
+      out = sum / cnt;
     }
-    double r = 0.0;
-    for (int i = 0; i < Q; ++i) {
-      ST::stf(B + i * P + c, out[i], rw<Q>(i));
-      r = (i == 0) ? out[0] : r + out[i];
+    if (i < Q) ST::stw(B + i * P + c, out);
+    // density of the refilled cell, summed in direction order
+    R r = (R)0;
+    for (int j = 0; j < Q; ++j) {
+      const R oj = __shfl_sync(FULL, out, j);
+      r = (j == 0) ? oj : r + oj;
     }
-    d.rho[c] = r;
+    if (lane == 0) d.rho[c] = SH ? 1.0 + (double)r : (double)r;
   }
 }
 
@@ -686,28 +1032,33 @@ __global__ void __launch_bounds__(256) k_excess_share(Dev d, Geom g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nf = ctrl->n_fill, ne = ctrl->n_empty;
-  FSL_GRID_LOOP(k, nf + ne) {
+  FSL_WARP_LOOP(k, ok, nf + ne) {
     const bool fill = k < nf;
-    const int c = fill ? d.l_fill[k] : d.l_empty[k - nf];
-    if (!fill && !(d.flags[c] & F_TO_GAS)) continue;
-    int x, y, z;
-    cell_xyz(g, c, x, y, z);
+    const int c = ok ? (fill ? d.l_fill[k] : d.l_empty[k - nf]) : 0;
+    const bool conv = ok && (fill || (d.flags[c] & F_TO_GAS));
+    int x = 0, y = 0, z = 0;
+    if (conv) cell_xyz(g, c, x, y, z);
     int nr = 0;
     for (int i = 1; i < Q; ++i) {
-      const int n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-      if (type_at(d.flags, n) != T_IF) continue;
-      nr++;
-      if (byte_or(d.claim, n, 1) == 0) {
-        unsigned slot = atomicAdd(&ctrl->n_recv, 1u);
-        d.l_recv[slot] = n;
+      int n = -1;
+      bool claimed = false;
+      if (conv) {
+        n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
+        if (type_at(d.flags, n) == T_IF) {
+          nr++;
+          claimed = byte_or(d.claim, n, 1) == 0;
+        }
       }
+      warp_append(claimed, n, &ctrl->n_recv, d.l_recv);
     }
-    const double mex = d.mex[c];
-    if (nr == 0) {
-      d.lost[c] += mex;
-      d.mex[c] = 0.0;
-    } else {
-      d.mex[c] = mex / (double)nr;
+    if (conv) {
+      const double mex = d.mex[c];
+      if (nr == 0) {
+        d.lost[c] += mex;
+        d.mex[c] = 0.0;
+      } else {
+        d.mex[c] = mex / (double)nr;
+      }
     }
   }
 }
@@ -746,8 +1097,9 @@ __device__ inline uint8_t iface_class(const Geom& g, const uint8_t* flags, int x
   return 0;
 }
 
-template <int Q>
+template <int Q, class ST>
 __global__ void __launch_bounds__(128) k_classify(Dev d, Geom g, Phys p) {
+  using R = typename ST::R;
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned a = ctrl->n_if, b = ctrl->n_new, e = ctrl->n_l2i;
@@ -760,7 +1112,7 @@ __global__ void __launch_bounds__(128) k_classify(Dev d, Geom g, Phys p) {
       int x, y, z;
       cell_xyz(g, c, x, y, z);
       nf |= iface_class<Q>(g, d.flags, x, y, z);
-      d.kappa[c] = (p.sigma != 0.0) ? curvature(g, d.flags, d.phi, x, y, z) : 0.0;
+      d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, d.phi, x, y, z) : 0.0;
     }
     d.flags[c] = nf;
   }
@@ -793,40 +1145,69 @@ __device__ inline int block_max(int v, int* sh) {
 }
 
 // End of step: optional trace record, counters for the next step, step++.
+// The trace reductions are split over kEndBlocks blocks (fixed partition,
+// fixed tree order); the last block to finish combines the partials in block
+// order and advances the counters.
+constexpr int kEndBlocks = 64;
 static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
   __shared__ double shd[256];
   __shared__ int shi[256];
+  __shared__ bool last;
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const int every = ctrl->trace_every;
-  if (every > 0 && ((ctrl->step + 1) % every) == 0) {
-    // column height at i = 0: sum_j,k phi / nz
-    double s = 0.0;
+  const bool tracing = every > 0 && ((ctrl->step + 1) % every) == 0;
+  double* part = d.red;                         // kEndBlocks column partials
+  int* ipart = reinterpret_cast<int*>(d.red + kEndBlocks);  // 2 x kEndBlocks maxima
+  if (tracing) {
     const int ncol = g.ny * g.nz;
-    for (int k = threadIdx.x; k < ncol; k += 256) s += d.phi[g.sx * k];
-    const double col = block_sum<256>(s, shd) / (double)g.nz;
-    // front: 1 + max i of an interface cell with j = 0
-    int best = -1;
-    for (int k = threadIdx.x; k < g.nx * g.nz; k += 256) {
+    const int chunk = (ncol + gridDim.x - 1) / gridDim.x;
+    const int k0 = blockIdx.x * chunk, k1 = min(ncol, k0 + chunk);
+    double s = 0.0;
+    int hbest = -1;
+    for (int k = k0 + threadIdx.x; k < k1; k += 256) {
+      const long long cidx = (long long)g.sx * k;   // cell (0, j, kz), k = j + ny kz
+      s += d.phi[cidx];
+      if ((d.flags[cidx] & F_TYPE) == T_IF) hbest = max(hbest, k % g.ny);
+    }
+    const double bs = block_sum<256>(s, shd);
+    const int bh = block_max<256>(hbest, shi);
+    // front: cells (i, 0, kz)
+    const int nrow = g.nx * g.nz;
+    const int rchunk = (nrow + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * rchunk, r1 = min(nrow, r0 + rchunk);
+    int fbest = -1;
+    for (int k = r0 + threadIdx.x; k < r1; k += 256) {
       const int i = k % g.nx, kz = k / g.nx;
-      if ((d.flags[i + g.sx * (g.ny * kz)] & F_TYPE) == T_IF) best = max(best, i);
+      if ((d.flags[i + (long long)g.sx * g.ny * kz] & F_TYPE) == T_IF) fbest = max(fbest, i);
     }
-    const int front = block_max<256>(best, shi) + 1;
-    best = -1;
-    for (int k = threadIdx.x; k < ncol; k += 256) {
-      const int j = k % g.ny;
-      if ((d.flags[g.sx * k] & F_TYPE) == T_IF) best = max(best, j);
-    }
-    const int height = block_max<256>(best, shi) + 1;
+    const int bf = block_max<256>(fbest, shi);
     if (threadIdx.x == 0) {
-      const int slot = ctrl->trace_count % kTraceCapacity;
-      d.trace[3 * slot + 0] = col;
-      d.trace[3 * slot + 1] = (double)front;
-      d.trace[3 * slot + 2] = (double)height;
-      ctrl->trace_count += 1;
+      part[blockIdx.x] = bs;
+      ipart[blockIdx.x] = bf;
+      ipart[kEndBlocks + blockIdx.x] = bh;
     }
   }
+  __threadfence();
+  if (threadIdx.x == 0) last = atomicAdd(&ctrl->pad[1], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
   if (threadIdx.x == 0) {
+    if (tracing) {
+      double col = 0.0;
+      int front = -1, height = -1;
+      for (int b = 0; b < (int)gridDim.x; ++b) {
+        col += *(volatile double*)&part[b];
+        front = max(front, *(volatile int*)&ipart[b]);
+        height = max(height, *(volatile int*)&ipart[kEndBlocks + b]);
+      }
+      const int slot = ctrl->trace_count % kTraceCapacity;
+      d.trace[3 * slot + 0] = col / (double)g.nz;
+      d.trace[3 * slot + 1] = (double)(front + 1);
+      d.trace[3 * slot + 2] = (double)(height + 1);
+      ctrl->trace_count += 1;
+    }
     ctrl->last[0] = ctrl->n_fill;
     ctrl->last[1] = ctrl->pad[0];
     ctrl->last[2] = ctrl->n_new;
@@ -834,6 +1215,8 @@ static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
     ctrl->n_if = ctrl->n_fill = ctrl->n_empty = 0;
     ctrl->n_new = ctrl->n_l2i = ctrl->n_recv = 0;
     ctrl->pad[0] = 0;
+    ctrl->pad[1] = 0;
+    __threadfence();
     ctrl->step += 1;
   }
 }
@@ -930,8 +1313,9 @@ __global__ void k_init_state(Dev d, Geom g, Phys p, int cur, const double* u0, d
   }
 }
 
-template <int Q>
+template <int Q, class ST>
 __global__ void k_init_classes(Dev d, Geom g, Phys p) {
+  using R = typename ST::R;
   const long long total = g.cells;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < total;
        c += (long long)gridDim.x * blockDim.x) {
@@ -941,7 +1325,7 @@ __global__ void k_init_classes(Dev d, Geom g, Phys p) {
     const uint8_t fl = d.flags[c];
     if ((fl & F_TYPE) != T_IF) continue;
     d.flags[c] = (uint8_t)((fl & ~(F_NF | F_NE)) | iface_class<Q>(g, d.flags, x, y, z));
-    d.kappa[c] = (p.sigma != 0.0) ? curvature(g, d.flags, d.phi, x, y, z) : 0.0;
+    d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, d.phi, x, y, z) : 0.0;
   }
 }
 
@@ -1037,8 +1421,7 @@ struct Kernels {
   // the buffer parity is read on the device from the step counter, so the
   // launch sequence is the same for every step (and graph-capturable)
   static cudaError_t step(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
-    dim3 b1(128), g1((g.nx + 127) / 128, g.ny, g.nz);
-    k_stream_collide<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
+    stream_collide(d, g, p, s);
     k_stream_collide_if<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
     k_fill<Q><<<kListBlocks, 256, 0, s>>>(d, g);
     k_empty<Q, ST><<<kListBlocks, 256, 0, s>>>(d, g);
@@ -1046,8 +1429,8 @@ struct Kernels {
     k_refill<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
     k_excess_share<Q><<<kListBlocks, 256, 0, s>>>(d, g);
     k_excess_gather<Q><<<kListBlocks, 256, 0, s>>>(d, g);
-    k_classify<Q><<<kListBlocks, 128, 0, s>>>(d, g, p);
-    k_end_step<<<1, 256, 0, s>>>(d, g);
+    k_classify<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
+    k_end_step<<<kEndBlocks, 256, 0, s>>>(d, g);
     return cudaGetLastError();
   }
   static cudaError_t init(const Dev& d, const Geom& g, const Phys& p, int cur, const double* u0,
@@ -1057,7 +1440,7 @@ struct Kernels {
     k_init_types<<<blocks, 256, 0, s>>>(d, g, d.phinew, d.claim, have_obst);
     k_init_close<Q><<<blocks, 256, 0, s>>>(d, g);
     k_init_state<Q, ST><<<blocks, 256, 0, s>>>(d, g, p, cur, u0, h_ref);
-    k_init_classes<Q><<<blocks, 128, 0, s>>>(d, g, p);
+    k_init_classes<Q, ST><<<blocks, 128, 0, s>>>(d, g, p);
     return cudaGetLastError();
   }
   static cudaError_t total_mass(const Dev& d, const Geom& g, const Phys&, int cur, double* out,
@@ -1077,8 +1460,19 @@ struct Kernels {
     k_export_plane<Q, ST><<<4 * 152, 256, 0, s>>>(d, g, cur, i, dst);
     return cudaGetLastError();
   }
+  static cudaError_t stream_collide(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
+    if constexpr (ST::kShift) {
+      dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
+      k_stream_collide_lp<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
+    } else {
+      dim3 b1(128), g1((g.nx + 127) / 128, g.ny, g.nz);
+      k_stream_collide<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
+    }
+    return cudaGetLastError();
+  }
   static const Launch* table() {
-    static const Launch L = {&step, &init, &total_mass, &max_velocity, &export_pdf, 11};
+    static const Launch L = {&step, &init, &total_mass, &max_velocity, &export_pdf,
+                             &stream_collide, 11};
     return &L;
   }
 };

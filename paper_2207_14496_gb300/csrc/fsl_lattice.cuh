@@ -69,6 +69,18 @@ __device__ __forceinline__ R dot3(R x, R y, R z) {
   return acc;
 }
 
+// Same with the coefficients as (unrolled-loop) values instead of template
+// arguments.
+template <class R>
+__device__ __forceinline__ R dot3r(int a, int b, int c, R x, R y, R z) {
+  R acc = R(0);
+  bool has = false;
+  if (a != 0) { acc = (a == 1) ? x : -x; has = true; }
+  if (b != 0) { R t = (b == 1) ? y : -y; acc = has ? acc + t : t; has = true; }
+  if (c != 0) { R t = (c == 1) ? z : -z; acc = has ? acc + t : t; has = true; }
+  return acc;
+}
+
 // ----------------------------------------------------------------- storage
 // Working representation inside the stream-collide kernel:
 //   FP64: f itself (operation order identical to a plain FP64 evaluation);
@@ -85,8 +97,19 @@ struct SF64 {
 };
 struct SF32 {
   using T = float;
+  using T2 = float2;
   using R = float;
   static constexpr bool kShift = true;
+  static constexpr float kScaleF = 1.0f;
+  // raw stored value(s) as float, in storage units (offset x kScaleF)
+  static __device__ __forceinline__ float ld1(const T* p) { return __ldg(p); }
+  static __device__ __forceinline__ float2 ld2(const T* p) {
+    return __ldg(reinterpret_cast<const float2*>(p));
+  }
+  static __device__ __forceinline__ void st1(T* p, float a) { *p = a; }
+  static __device__ __forceinline__ void st2(T* p, float a, float b) {
+    *reinterpret_cast<float2*>(p) = make_float2(a, b);
+  }
   static __device__ __forceinline__ R ldw(const T* p) { return __ldg(p); }
   static __device__ __forceinline__ void stw(T* p, R v) { *p = v; }
   static __device__ __forceinline__ double ldf(const T* p, double w) { return w + (double)__ldg(p); }
@@ -96,9 +119,19 @@ struct SF32 {
 // offsets up to 2 fit the format's range.
 struct SF16 {
   using T = __half;
+  using T2 = __half2;
   using R = float;
   static constexpr bool kShift = true;
   static constexpr float kScale = 32768.0f, kInv = 1.0f / 32768.0f;
+  static constexpr float kScaleF = 32768.0f;
+  static __device__ __forceinline__ float ld1(const T* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ float2 ld2(const T* p) {
+    return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+  }
+  static __device__ __forceinline__ void st1(T* p, float a) { *p = __float2half_rn(a); }
+  static __device__ __forceinline__ void st2(T* p, float a, float b) {
+    *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
+  }
   static __device__ __forceinline__ R ldw(const T* p) { return __half2float(__ldg(p)) * kInv; }
   static __device__ __forceinline__ void stw(T* p, R v) { *p = __float2half_rn(v * kScale); }
   static __device__ __forceinline__ double ldf(const T* p, double w) {
@@ -110,8 +143,18 @@ struct SF16 {
 };
 struct SBF16 {
   using T = __nv_bfloat16;
+  using T2 = __nv_bfloat162;
   using R = float;
   static constexpr bool kShift = true;
+  static constexpr float kScaleF = 1.0f;
+  static __device__ __forceinline__ float ld1(const T* p) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ float2 ld2(const T* p) {
+    return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
+  }
+  static __device__ __forceinline__ void st1(T* p, float a) { *p = __float2bfloat16_rn(a); }
+  static __device__ __forceinline__ void st2(T* p, float a, float b) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+  }
   static __device__ __forceinline__ R ldw(const T* p) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ void stw(T* p, R v) { *p = __float2bfloat16_rn(v); }
   static __device__ __forceinline__ double ldf(const T* p, double w) {

@@ -76,6 +76,8 @@ _lib.fsl_destroy.argtypes = [_VP]
 _lib.fsl_lattice_table.argtypes = [ctypes.c_int, _VP, _VP]
 _lib.fsl_launches_per_step.argtypes = [_VP]
 _lib.fsl_launches_per_step.restype = ctypes.c_int
+_lib.fsl_kernel_stats.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
+_lib.fsl_kernel_stats.restype = ctypes.c_int
 _lib.fsl_status_string.argtypes = [ctypes.c_int]
 _lib.fsl_status_string.restype = ctypes.c_char_p
 _lib.fsl_last_error.restype = ctypes.c_char_p
@@ -86,8 +88,9 @@ for _name in ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", 
 
 EXPORTED = ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "fsl_observe",
             "fsl_set_trace", "fsl_trace_capacity", "fsl_state_bytes", "fsl_save", "fsl_load",
-            "fsl_destroy", "fsl_lattice_table", "fsl_launches_per_step", "fsl_status_string",
-            "fsl_last_error")
+            "fsl_destroy", "fsl_lattice_table", "fsl_launches_per_step", "fsl_kernel_stats",
+            "fsl_status_string", "fsl_last_error")
+KERNEL_STREAM_COLLIDE = 1
 
 
 class FslError(RuntimeError):
@@ -190,6 +193,12 @@ class Sim:
 
     def launches_per_step(self) -> int:
         return int(_lib.fsl_launches_per_step(self.h))
+
+    def kernel_stats(self, reps: int = 10, kernel: int = KERNEL_STREAM_COLLIDE) -> dict:
+        out = np.zeros(4)
+        _check(_lib.fsl_kernel_stats(self.h, int(kernel), int(reps), _ptr(out)), "fsl_kernel_stats")
+        return dict(ms=float(out[0]), bytes=float(out[1]), n_liquid=int(out[2]),
+                    n_interface=int(out[3]))
 
     def init_fill(self, phi, u0=None, obstacle=None, h_ref=float("nan")):
         phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(-1))
