@@ -177,6 +177,29 @@ int fsl_launches_per_step(const fsl_handle* h);
 enum { FSL_KERNEL_STREAM_COLLIDE = 1 };
 fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4);
 
+/* Total mass of a state held in caller-owned device arrays, for callers that
+ * cannot allocate device memory when they need it (during a CUDA graph
+ * capture, inside a host callback or another allocator, or under a fixed
+ * device-memory budget).  The paper has no counterpart: this is a library
+ * convenience.  It allocates nothing: its reduction scratch is a static
+ * 16 KiB device array inside the library, shared by all calls; calls whose
+ * kernels overlap on the GPU race on it.  The first call on each device
+ * looks up that array (make it before any stream capture).
+ *   cfg: lattice, precision, nx/ny/nz (other fields ignored);
+ *   d_pdf: device, q planes of nx*ny*nz stored values in the dense layout
+ *     (x fastest, no row padding) and the storage of cfg->precision (FP64:
+ *     f_i; FP32: f_i - w_i; FP16: (f_i - w_i) * 2^15; BF16: f_i - w_i);
+ *   d_types: device, nx*ny*nz type codes (0 gas, 1 interface, 2 liquid, 3 obstacle);
+ *   d_mass: device, nx*ny*nz doubles (read in interface cells);
+ *   d_lost: device, nx*ny*nz doubles of lost mass per cell, or NULL;
+ *   d_out: device, one double: sum of liquid zeroth moments + interface mass + lost mass;
+ *   cuda_stream: the stream to run on (cudaStream_t as void*).
+ * Asynchronous.  FSL_ERR_ARG for a null pointer, a bad lattice or size, or
+ * more than 33554432 cells (the scratch limit; message in fsl_last_error). */
+fsl_status fsl_total_mass_noalloc(const fsl_config* cfg, const void* d_pdf,
+                                  const unsigned char* d_types, const double* d_mass,
+                                  const double* d_lost, double* d_out, void* cuda_stream);
+
 /* Static description of a status code; last CUDA error text of this thread. */
 const char* fsl_status_string(fsl_status s);
 const char* fsl_last_error(void);

@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfsl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-UNITS = {"fsl_api.cu": []}
+UNITS = {"fsl_api.cu": [], "fsl_noalloc.cu": []}
 for _p in ("fp64", "fp32", "fp16", "bf16"):
     for _q in (19, 27):
         UNITS[f"k_{_p}_q{_q}.cu"] = ["-fmad=false"] if _p == "fp64" else []

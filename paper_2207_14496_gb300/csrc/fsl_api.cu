@@ -132,6 +132,8 @@ const Launch* pick(int precision, int q) {
 
 }  // namespace
 
+void fsl::set_error_text(const char* msg) { g_err = msg ? msg : ""; }
+
 size_t fsl::storage_bytes(int precision) {
   return precision == FSL_FP64 ? 8 : precision == FSL_FP32 ? 4 : 2;
 }

@@ -123,4 +123,7 @@ const Launch* launch_bf16_q27();
 
 size_t storage_bytes(int precision);
 
+// text returned by fsl_last_error() on this thread
+void set_error_text(const char* msg);
+
 }  // namespace fsl

@@ -78,6 +78,8 @@ _lib.fsl_launches_per_step.argtypes = [_VP]
 _lib.fsl_launches_per_step.restype = ctypes.c_int
 _lib.fsl_kernel_stats.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
 _lib.fsl_kernel_stats.restype = ctypes.c_int
+_lib.fsl_total_mass_noalloc.argtypes = [ctypes.POINTER(fsl_config), _VP, _VP, _VP, _VP, _VP, _VP]
+_lib.fsl_total_mass_noalloc.restype = ctypes.c_int
 _lib.fsl_status_string.argtypes = [ctypes.c_int]
 _lib.fsl_status_string.restype = ctypes.c_char_p
 _lib.fsl_last_error.restype = ctypes.c_char_p
@@ -89,7 +91,7 @@ for _name in ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", 
 EXPORTED = ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "fsl_observe",
             "fsl_set_trace", "fsl_trace_capacity", "fsl_state_bytes", "fsl_save", "fsl_load",
             "fsl_destroy", "fsl_lattice_table", "fsl_launches_per_step", "fsl_kernel_stats",
-            "fsl_status_string", "fsl_last_error")
+            "fsl_status_string", "fsl_last_error", "fsl_total_mass_noalloc")
 KERNEL_STREAM_COLLIDE = 1
 
 
