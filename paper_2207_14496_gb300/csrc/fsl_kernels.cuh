@@ -381,6 +381,7 @@ __global__ void __launch_bounds__(128) k_stream_collide_lp(Dev d, Geom g, Phys p
   if (__any_sync(FULL, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
 }
 
+
 // ------------------------------------------------------------ stream-collide
 // Pass over all cells: liquid cells stream and collide here; interface cells
 // are compacted (warp ballot) into l_if for k_stream_collide_if.
@@ -526,38 +527,45 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
 // ------------------------------------------------------------ conversion
 
 
+// lane i of a warp examines direction i of the warp's cell (warp-per-cell
+// loops); lanes >= Q stay idle but take part in the ballots
+#define FSL_WARP_PER_ITEM(k, n)                                                     \
+  for (unsigned k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < (n);          \
+       k += (gridDim.x * blockDim.x) >> 5)
+
 template <int Q>
 __global__ void __launch_bounds__(256) k_fill(Dev d, Geom g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nif = ctrl->n_if, nfill = ctrl->n_fill;
-  FSL_WARP_LOOP(k, ok, nif + nfill) {
-    if (ok && k < nif) {
-      const int c = d.l_if[k];
-      d.phi[c] = d.phinew[c];
-    }
-    const bool filling = ok && k >= nif;
-    int x = 0, y = 0, z = 0;
-    if (filling) cell_xyz(g, d.l_fill[k - nif], x, y, z);
-    for (int i = 1; i < Q; ++i) {
-      int n = -1;
-      bool created = false;
-      if (filling) {
-        n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-        if (n >= 0) {
-          if ((d.flags[n] & F_TYPE) == T_GAS) {
-            const uint8_t old = byte_or(d.flags, n, (uint8_t)(F_NEW | T_IF));
-            if (!(old & F_NEW)) {
-              d.phi[n] = 0.0;
-              d.mass[n] = 0.0;
-              created = true;
-            }
+  // commit the fill levels computed by the stream-collide pass
+  FSL_GRID_LOOP(k, nif) {
+    const int c = d.l_if[k];
+    d.phi[c] = d.phinew[c];
+  }
+  // gas neighbours of filled cells become new interface cells; a neighbour
+  // about to empty is kept (filling wins)
+  const int lane = threadIdx.x & 31;
+  FSL_WARP_PER_ITEM(k, nfill) {
+    int x, y, z;
+    cell_xyz(g, d.l_fill[k], x, y, z);
+    int n = -1;
+    bool created = false;
+    if (lane >= 1 && lane < Q) {
+      n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
+      if (n >= 0) {
+        if ((d.flags[n] & F_TYPE) == T_GAS) {
+          const uint8_t old = byte_or(d.flags, n, (uint8_t)(F_NEW | T_IF));
+          if (!(old & F_NEW)) {
+            d.phi[n] = 0.0;
+            d.mass[n] = 0.0;
+            created = true;
           }
-          if (d.flags[n] & F_TO_GAS) byte_and(d.flags, n, F_TO_GAS);
         }
+        if (d.flags[n] & F_TO_GAS) byte_and(d.flags, n, F_TO_GAS);
       }
-      warp_append(created, n, &ctrl->n_new, d.l_new);
     }
+    warp_append(created, n, &ctrl->n_new, d.l_new);
   }
 }
 
@@ -570,35 +578,34 @@ __global__ void __launch_bounds__(256) k_empty(Dev d, Geom g) {
   const int cur = ctrl->step & 1;
   const typename ST::T* A = (const typename ST::T*)d.pdf[cur];
   const unsigned ne = ctrl->n_empty;
-  FSL_WARP_LOOP(k, ok, ne) {
-    const int c = ok ? d.l_empty[k] : 0;
-    const bool emptying = ok && (d.flags[c] & F_TO_GAS);
-    int x = 0, y = 0, z = 0;
-    if (emptying) cell_xyz(g, c, x, y, z);
-    for (int i = 1; i < Q; ++i) {
-      int n = -1;
-      bool won = false;
-      if (emptying) {
-        n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-        if (n >= 0 && (d.flags[n] & F_TYPE) == T_LIQ &&
-            byte_retype(d.flags, n, T_LIQ, T_IF, &ctrl->timeout)) {
-          // the liquid cell's density of this step, recomputed exactly as the
-          // stream-collide pass obtained it
-          int nx_, ny_, nz_;
-          cell_xyz(g, n, nx_, ny_, nz_);
-          Nbr nb;
-          nb.setup(g, nx_, ny_, nz_);
-          R fin[Q], rho, drho;
-          pull_liquid<Q, ST>(A, g.plane, d.flags, nb, n, (d.flags[n] & F_NEAR_OBST) != 0, fin);
-          density<Q, SH, R>(fin, rho, drho);
-          d.rho[n] = (double)rho;
-          d.mass[n] = (double)rho;
-          d.phi[n] = 1.0;
-          won = true;
-        }
+  const int lane = threadIdx.x & 31;
+  FSL_WARP_PER_ITEM(k, ne) {
+    const int c = d.l_empty[k];
+    if (!(d.flags[c] & F_TO_GAS)) continue;  // kept by a filling neighbour (warp-uniform)
+    int x, y, z;
+    cell_xyz(g, c, x, y, z);
+    int n = -1;
+    bool won = false;
+    if (lane >= 1 && lane < Q) {
+      n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
+      if (n >= 0 && (d.flags[n] & F_TYPE) == T_LIQ &&
+          byte_retype(d.flags, n, T_LIQ, T_IF, &ctrl->timeout)) {
+        // the liquid cell's density of this step, recomputed exactly as the
+        // stream-collide pass obtained it
+        int nx_, ny_, nz_;
+        cell_xyz(g, n, nx_, ny_, nz_);
+        Nbr nb;
+        nb.setup(g, nx_, ny_, nz_);
+        R fin[Q], rho, drho;
+        pull_liquid<Q, ST>(A, g.plane, d.flags, nb, n, (d.flags[n] & F_NEAR_OBST) != 0, fin);
+        density<Q, SH, R>(fin, rho, drho);
+        d.rho[n] = (double)rho;
+        d.mass[n] = (double)rho;
+        d.phi[n] = 1.0;
+        won = true;
       }
-      warp_append(won, n, &ctrl->n_l2i, d.l_l2i);
     }
+    warp_append(won, n, &ctrl->n_l2i, d.l_l2i);
   }
 }
 
@@ -1032,26 +1039,25 @@ __global__ void __launch_bounds__(256) k_excess_share(Dev d, Geom g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nf = ctrl->n_fill, ne = ctrl->n_empty;
-  FSL_WARP_LOOP(k, ok, nf + ne) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  FSL_WARP_PER_ITEM(k, nf + ne) {
     const bool fill = k < nf;
-    const int c = ok ? (fill ? d.l_fill[k] : d.l_empty[k - nf]) : 0;
-    const bool conv = ok && (fill || (d.flags[c] & F_TO_GAS));
-    int x = 0, y = 0, z = 0;
-    if (conv) cell_xyz(g, c, x, y, z);
-    int nr = 0;
-    for (int i = 1; i < Q; ++i) {
-      int n = -1;
-      bool claimed = false;
-      if (conv) {
-        n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-        if (type_at(d.flags, n) == T_IF) {
-          nr++;
-          claimed = byte_or(d.claim, n, 1) == 0;
-        }
-      }
-      warp_append(claimed, n, &ctrl->n_recv, d.l_recv);
+    const int c = fill ? d.l_fill[k] : d.l_empty[k - nf];
+    if (!fill && !(d.flags[c] & F_TO_GAS)) continue;  // not converted (warp-uniform)
+    int x, y, z;
+    cell_xyz(g, c, x, y, z);
+    int n = -1;
+    bool recv = false, claimed = false;
+    if (lane >= 1 && lane < Q) {
+      n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
+      recv = type_at(d.flags, n) == T_IF;
+      if (recv) claimed = byte_or(d.claim, n, 1) == 0;
     }
-    if (conv) {
+    // receivers counted per direction (with multiplicity)
+    const int nr = __popc(__ballot_sync(FULL, recv));
+    warp_append(claimed, n, &ctrl->n_recv, d.l_recv);
+    if (lane == 0) {
       const double mex = d.mex[c];
       if (nr == 0) {
         d.lost[c] += mex;
@@ -1063,22 +1069,36 @@ __global__ void __launch_bounds__(256) k_excess_share(Dev d, Geom g) {
   }
 }
 
+// Each receiver gathers the shares of its converted neighbours, summed in
+// direction order.
 template <int Q>
 __global__ void __launch_bounds__(256) k_excess_gather(Dev d, Geom g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nr = ctrl->n_recv;
-  FSL_GRID_LOOP(k, nr) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  FSL_WARP_PER_ITEM(k, nr) {
     const int r = d.l_recv[k];
     int x, y, z;
     cell_xyz(g, r, x, y, z);
-    double sum = 0.0;
-    for (int i = 1; i < Q; ++i) {
-      const int n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-      if (n >= 0 && (d.flags[n] & (F_TO_LIQ | F_TO_GAS))) sum += d.mex[n];
+    double v = 0.0;
+    bool conv = false;
+    if (lane >= 1 && lane < Q) {
+      const int n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
+      conv = n >= 0 && (d.flags[n] & (F_TO_LIQ | F_TO_GAS));
+      if (conv) v = d.mex[n];
     }
-    d.mass[r] = d.mass[r] + sum;
-    d.phi[r] = d.mass[r] / d.rho[r];
+    const unsigned cm = __ballot_sync(FULL, conv);
+    double sum = 0.0;
+    for (int j = 1; j < Q; ++j) {
+      const double vj = __shfl_sync(FULL, v, j);
+      if ((cm >> j) & 1u) sum += vj;
+    }
+    if (lane == 0) {
+      d.mass[r] = d.mass[r] + sum;
+      d.phi[r] = d.mass[r] / d.rho[r];
+    }
   }
 }
 
@@ -1193,15 +1213,25 @@ static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
   __syncthreads();
   if (!last) return;
   __threadfence();
+  if (tracing) {
+    const bool in = (int)threadIdx.x < (int)gridDim.x;
+    const double cp = in ? *(volatile double*)&part[threadIdx.x] : 0.0;
+    const int fp = in ? *(volatile int*)&ipart[threadIdx.x] : -1;
+    const int hp = in ? *(volatile int*)&ipart[kEndBlocks + threadIdx.x] : -1;
+    const double col_all = block_sum<256>(cp, shd);
+    const int front_all = block_max<256>(fp, shi);
+    const int height_all = block_max<256>(hp, shi);
+    if (threadIdx.x == 0) {
+      shd[0] = col_all;
+      shi[0] = front_all;
+      shi[1] = height_all;
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
     if (tracing) {
-      double col = 0.0;
-      int front = -1, height = -1;
-      for (int b = 0; b < (int)gridDim.x; ++b) {
-        col += *(volatile double*)&part[b];
-        front = max(front, *(volatile int*)&ipart[b]);
-        height = max(height, *(volatile int*)&ipart[kEndBlocks + b]);
-      }
+      const double col = shd[0];
+      const int front = shi[0], height = shi[1];
       const int slot = ctrl->trace_count % kTraceCapacity;
       d.trace[3 * slot + 0] = col / (double)g.nz;
       d.trace[3 * slot + 1] = (double)(front + 1);

@@ -103,6 +103,7 @@ struct SF32 {
   static constexpr float kScaleF = 1.0f;
   // raw stored value(s) as float, in storage units (offset x kScaleF)
   static __device__ __forceinline__ float ld1(const T* p) { return __ldg(p); }
+  static __device__ __forceinline__ float ld1s(const T* p) { return *p; }
   static __device__ __forceinline__ float2 ld2(const T* p) {
     return __ldg(reinterpret_cast<const float2*>(p));
   }
@@ -125,6 +126,7 @@ struct SF16 {
   static constexpr float kScale = 32768.0f, kInv = 1.0f / 32768.0f;
   static constexpr float kScaleF = 32768.0f;
   static __device__ __forceinline__ float ld1(const T* p) { return __half2float(__ldg(p)); }
+  static __device__ __forceinline__ float ld1s(const T* p) { return __half2float(*p); }
   static __device__ __forceinline__ float2 ld2(const T* p) {
     return __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
   }
@@ -148,6 +150,7 @@ struct SBF16 {
   static constexpr bool kShift = true;
   static constexpr float kScaleF = 1.0f;
   static __device__ __forceinline__ float ld1(const T* p) { return __bfloat162float(__ldg(p)); }
+  static __device__ __forceinline__ float ld1s(const T* p) { return __bfloat162float(*p); }
   static __device__ __forceinline__ float2 ld2(const T* p) {
     return __bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)));
   }
