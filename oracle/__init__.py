@@ -54,6 +54,8 @@ class _Config(ctypes.Structure):
         ("p_v", ctypes.c_double),
         ("eps", ctypes.c_double),
         ("options", ctypes.c_uint),
+        ("les_cs", ctypes.c_double),
+        ("free_slip", ctypes.c_int * 3),
     ]
 
 
@@ -122,7 +124,8 @@ class Oracle:
 
     ``params`` keys: q (19|27), collision ('srt'|'trt'), magic, refill
     ('eq'|'eq_neq'|'geq'|'ext'|'avg'), shape (nx, ny, nz), periodic (3 bools),
-    nu, g (3), sigma, p_v, eps, options (int bit set).
+    nu, g (3), sigma, p_v, eps, options (int bit set), les_cs (Smagorinsky
+    constant, 0 = off), free_slip (3 bools: walls of that axis are free-slip).
     """
 
     def __init__(self, params: dict):
@@ -145,6 +148,10 @@ class Oracle:
         c.p_v = float(params.get("p_v", 1.0 / 3.0))
         c.eps = float(params.get("eps", 1e-2))
         c.options = int(params.get("options", 0))
+        c.les_cs = float(params.get("les_cs", 0.0))
+        fs = params.get("free_slip", (False, False, False))
+        for a in range(3):
+            c.free_slip[a] = 1 if fs[a] else 0
         self.q = c.q
         self.shape = (c.nx, c.ny, c.nz)
         self.N = c.nx * c.ny * c.nz

@@ -92,12 +92,15 @@ typedef struct {
   double p_v;    /* volume (atmospheric) pressure, 1/3 */
   double eps;    /* conversion threshold epsilon_phi */
   unsigned options;
+  double les_cs;   /* Smagorinsky constant C_S (Sec. 2.1); 0 = no turbulence model */
+  int free_slip[3]; /* non-periodic axis: 1 = free-slip (specular) walls instead of no-slip */
 } orc_config;
 
 typedef struct {
   orc_config c;
   int q;
   int cx[27], cy[27], cz[27], opp[27];
+  int mirror[27][8]; /* direction with the components in mask (bit a = axis a) negated */
   double w[27];
   long N;
   double tau, omega, lam_e, lam_o;
@@ -133,6 +136,15 @@ static const int DIRS[27][3] = {
 static void setup_lattice(orc_state *s) {
   int q = s->c.q;
   s->q = q;
+  for (int i = 0; i < q; ++i)
+    for (int m = 0; m < 8; ++m) {
+      int c[3] = {DIRS[i][0], DIRS[i][1], DIRS[i][2]};
+      for (int a = 0; a < 3; ++a)
+        if (m & (1 << a)) c[a] = -c[a];
+      s->mirror[i][m] = -1;
+      for (int j = 0; j < q; ++j)
+        if (DIRS[j][0] == c[0] && DIRS[j][1] == c[1] && DIRS[j][2] == c[2]) s->mirror[i][m] = j;
+    }
   for (int i = 0; i < q; ++i) {
     s->cx[i] = DIRS[i][0];
     s->cy[i] = DIRS[i][1];
@@ -178,6 +190,37 @@ static long neighbour(const orc_state *s, long x, int d, int mult) {
 }
 
 static int type_of(const orc_state *s, long x) { return x < 0 ? ORC_OBST : s->type[x]; }
+
+/* Where the PDF f_i arriving at cell x comes from.  Normally the cell x - c_i
+ * with direction i.  Across free-slip walls (Sec. 2.1: specular reflection,
+ * the wall-normal velocity component reversed) the PDF left the cell x - c_i
+ * with the crossed components removed, in the mirrored direction.  Returns
+ * -1 for a no-slip wall or an obstacle (halfway bounce-back), else the source
+ * cell, with *dir its direction. */
+static long pdf_source(const orc_state *s, long x, int i, int *dir) {
+  long p0, p1, p2;
+  cell_coords(s, x, &p0, &p1, &p2);
+  long p[3] = {p0, p1, p2};
+  long n[3] = {s->c.nx, s->c.ny, s->c.nz};
+  int c[3] = {s->cx[i], s->cy[i], s->cz[i]};
+  int crossed = 0;
+  long q[3];
+  for (int a = 0; a < 3; ++a) {
+    q[a] = p[a] - c[a];
+    if ((q[a] < 0 || q[a] >= n[a]) && !s->c.periodic[a]) crossed |= 1 << a;
+  }
+  *dir = i;
+  if (crossed) {
+    for (int a = 0; a < 3; ++a)
+      if ((crossed & (1 << a)) && !s->c.free_slip[a]) return -1;
+    for (int a = 0; a < 3; ++a)
+      if (crossed & (1 << a)) q[a] = p[a];
+    *dir = s->mirror[i][crossed];
+  }
+  long y = cell_index(s, q[0], q[1], q[2]);
+  if (y >= 0 && s->type[y] == ORC_OBST) return -1;
+  return y;
+}
 static int is_fluid_type(int t) { return t == ORC_LIQUID || t == ORC_IFACE; }
 
 /* ------------------------------------------------------------ LBM pieces */
@@ -574,11 +617,12 @@ static void step_once(orc_state *s) {
       rho_g = 3.0 * pg; /* rho_G = p_G / c_s^2 */
     }
     for (int i = 0; i < q; ++i) {
-      long y = neighbour(s, x, i, -1); /* the PDF f_i arrives from x - c_i */
+      int di;
+      long y = pdf_source(s, x, i, &di); /* the PDF f_i arrives from x - c_i */
       int t = type_of(s, y);
       int io = s->opp[i];
       if (is_fluid_type(t)) {
-        fin[i] = s->f[i * N + y];
+        fin[i] = s->f[di * N + y];
       } else if (t == ORC_OBST) {
         fin[i] = s->f[io * N + x]; /* halfway bounce-back */
       } else {
@@ -592,14 +636,16 @@ static void step_once(orc_state *s) {
       /* Eq. nm-fslbm-mass-flux, summed as in Eq. rs-mass-change */
       double dm = 0.0;
       for (int i = 1; i < q; ++i) {
-        long y = neighbour(s, x, i, 1);
+        /* the cell exchanging PDFs with x along c_i: x + c_i, or its mirror
+         * image across a free-slip wall; f_in is what arrives from it */
+        int io = s->opp[i], dj;
+        long y = pdf_source(s, x, io, &dj);
         int t = type_of(s, y);
-        int io = s->opp[i];
         double d = 0.0;
         if (t == ORC_LIQUID) {
-          d = s->f[io * N + y] - s->f[i * N + x];
+          d = s->f[dj * N + y] - s->f[i * N + x];
         } else if (t == ORC_IFACE) {
-          double f_in = s->f[io * N + y], f_out = s->f[i * N + x];
+          double f_in = s->f[dj * N + y], f_out = s->f[i * N + x];
           double br = f_in - f_out;
           if (thurey) {
             int cx_ = s->cls[x], cy_ = s->cls[y];
@@ -630,13 +676,35 @@ static void step_once(orc_state *s) {
       fe[i] = feq(s, i, rho, ux, uy, uz);
       fg[i] = guo(s, i, ux, uy, uz, Fx, Fy, Fz);
     }
+    double omega = s->omega, lam_e = s->lam_e, lam_o = s->lam_o;
+    if (s->c.les_cs > 0.0) {
+      /* Smagorinsky model (Sec. 2.1, Eqs. nm-lbm-turbulence-viscosity to
+       * nm-lbm-turublence-relaxation-time): Q_ab = sum_i c_ia c_ib (f_i - f_i^eq),
+       * Qbar = sqrt(2 sum_ab Q_ab Q_ab),
+       * tau = tau0 + (sqrt(tau0^2 + 2 sqrt(2) C_S^2 Qbar / (rho c_s^4)) - tau0) / 2 */
+      int c[27][3];
+      for (int i = 0; i < q; ++i) { c[i][0] = s->cx[i]; c[i][1] = s->cy[i]; c[i][2] = s->cz[i]; }
+      double qq = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double Qab = 0.0;
+          for (int i = 0; i < q; ++i) Qab += (double)(c[i][a] * c[i][b]) * (fin[i] - fe[i]);
+          qq += Qab * Qab;
+        }
+      double qbar = sqrt(2.0 * qq);
+      double t0 = s->tau, cs = s->c.les_cs;
+      double tau = t0 + 0.5 * (sqrt(t0 * t0 + 2.0 * sqrt(2.0) * cs * cs * qbar * 9.0 / rho) - t0);
+      omega = 1.0 / tau;
+      lam_e = omega;
+      lam_o = 1.0 / (0.5 + s->c.magic / (1.0 / lam_e - 0.5));
+    }
     if (!s->c.trt) {
       /* SRT: f* = f - omega (f - f^eq) + (1 - omega/2) F_i */
-      double om = s->omega, pre = 1.0 - 0.5 * s->omega;
+      double om = omega, pre = 1.0 - 0.5 * omega;
       for (int i = 0; i < q; ++i) s->fn[i * N + x] = fin[i] - om * (fin[i] - fe[i]) + pre * fg[i];
     } else {
       /* TRT: symmetric parts relax with lam_e, antisymmetric with lam_o */
-      double le = s->lam_e, lo = s->lam_o;
+      double le = lam_e, lo = lam_o;
       double pe = 1.0 - 0.5 * le, po = 1.0 - 0.5 * lo;
       s->fn[x] = fin[0] - le * (fin[0] - fe[0]) + pe * fg[0];
       for (int i = 1; i < q; i += 2) {

@@ -132,6 +132,26 @@ def dam_break(nx=512, ny=256, nz=16, width=128, height=128, g=2e-5, nu=5e-4,
                 obstacle=None, h_ref=float(height), width=width, height=height)
 
 
+def paper_dam_break(W: int = 50, refill: str = "eq", collision: str = "srt", les_cs: float = 0.1,
+                    omega: float = 1.9995, ga: float = 1.83e9, bo: float = 445.0):
+    """The paper's rectangular dam break (Sec. 4.2): column W x 2W at the left
+    wall of a 15W x 4W x 1 domain, free-slip walls, relaxation rate 1.9995,
+    Smagorinsky C_S = 0.1, gravity from the Galilei number Ga = g W^3 / nu^2,
+    surface tension from the Bond number Bo = g W^2 / sigma (rho = 1),
+    hydrostatic pressure with p = p0 at the column top."""
+    nu = (1.0 / 3.0) * (1.0 / omega - 0.5)
+    g = ga * nu * nu / float(W) ** 3
+    sigma = g * float(W) ** 2 / bo
+    H = 2 * W
+    params = _base(q=19, collision=collision, refill=refill, shape=(15 * W, 2 * H, 1),
+                   periodic=(False, False, True), nu=nu, g=(0.0, -g, 0.0), sigma=sigma)
+    params["free_slip"] = (True, True, False)
+    params["les_cs"] = les_cs
+    phi = box_fill(15 * W, 2 * H, 1, W, H)
+    return dict(name=f"paper_dam_break_W{W}", params=params, phi=phi, u0=None, obstacle=None,
+                h_ref=float(H), width=W, height=H, g=g)
+
+
 # Ohnesorge number of the paper's drop impact (Sec. 4.5): Oh = mu / sqrt(sigma rho D)
 DROP_OH = 0.0384
 

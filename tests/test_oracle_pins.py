@@ -469,3 +469,89 @@ def _mean_state(o, idx, new):
         us += (fy @ c) / r
         n += 1
     return rs / n, us / n
+
+
+# ------------------------------------------------------------------ free-slip and LES
+def test_free_slip_channel_is_plug_flow():
+    """Free-slip walls (Sec. 2.1: specular reflection) exert no tangential
+    stress: a liquid channel driven along x by a body force accelerates as a
+    plug, uniformly in y (no-slip walls would shear it).  The initial stored
+    PDFs are f^eq(rho, 0), whose moment velocity is -g/2, so after t steps
+    u_x = g (t - 1/2)."""
+    ny, g, steps = 12, 1e-5, 300
+    w = inputs.poiseuille(ny=ny, nx=4, g=g, nu=0.05, collision="srt")
+    w["params"]["free_slip"] = (False, True, False)
+    o = oracle.Oracle(w["params"])
+    o.init_fill(w["phi"])
+    o.step(steps)
+    f = o.pdfs()
+    c, _, _ = o.lattice()
+    rho = f.sum(0)
+    ux = np.einsum("i,izyx->zyx", c[:, 0].astype(float), f) / rho - 0.5 * g
+    prof = ux[0, :, 0]
+    assert np.ptp(prof) < 1e-15
+    assert abs(prof.mean() - g * (steps - 0.5)) < 1e-15 * steps
+    # the same channel with no-slip walls is sheared
+    w["params"]["free_slip"] = (False, False, False)
+    o2 = oracle.Oracle(w["params"])
+    o2.init_fill(w["phi"])
+    o2.step(steps)
+    f2 = o2.pdfs()
+    ux2 = np.einsum("i,izyx->zyx", c[:, 0].astype(float), f2) / f2.sum(0) - 0.5 * g
+    assert np.ptp(ux2[0, :, 0]) > 1e-4 * g * steps
+
+
+@pytest.mark.parametrize("scheme", ["eq", "geq"])
+def test_free_slip_dam_break_conserves_mass(scheme):
+    """Across free-slip walls the mass flux pairs a cell with its mirror
+    image; the exchange stays antisymmetric, so the total mass is conserved
+    through conversions (paper's dam break walls, Sec. 4.2, with LES)."""
+    w = inputs.dam_break(nx=60, ny=40, nz=1, width=16, height=24, g=2e-4, nu=5e-3, refill=scheme)
+    w["params"]["periodic"] = (False, False, True)
+    w["params"]["free_slip"] = (True, True, False)
+    w["params"]["les_cs"] = 0.1
+    o = oracle.Oracle(w["params"])
+    o.init_fill(w["phi"], h_ref=w["h_ref"])
+    m0 = exact_mass(o)
+    conv = 0
+    for _ in range(250):
+        o.step(1)
+        conv += sum(o.last_counts())
+    assert conv > 100 and o.unstable_step < 0
+    assert abs(exact_mass(o) - m0) <= 4 * 250 * EPS * m0
+    assert closed_layer_ok(o)
+
+
+def test_smagorinsky_poiseuille_matches_eddy_viscosity_closure():
+    """Smagorinsky model (Sec. 2.1): in a simple shear with rate gamma the
+    first-order non-equilibrium momentum flux is Q_xy = Q_yx = -rho c_s^2 tau
+    gamma, so Qbar = 2 rho c_s^2 tau gamma and the relaxation-time equation
+    tau = tau0 + (sqrt(tau0^2 + 2 sqrt(2) C^2 Qbar / (rho c_s^4)) - tau0)/2
+    solves to tau = tau0 + 3 sqrt(2) C^2 gamma, i.e. nu = nu0 + sqrt(2) C^2
+    gamma.  The steady body-force channel must then follow
+    nu(y) u'(y) = g (H/2 - y), whose solution is computed here by quadrature."""
+    ny, nx, g, nu0, cs = 16, 4, 2e-5, 0.005, 0.4
+    w = inputs.poiseuille(ny=ny, nx=nx, g=g, nu=nu0, collision="trt")
+    w["params"]["les_cs"] = cs
+    o = oracle.Oracle(w["params"])
+    o.init_fill(w["phi"])
+    o.step(30000)
+    f = o.pdfs()
+    c, _, _ = o.lattice()
+    ux = np.einsum("i,izyx->zyx", c[:, 0].astype(float), f) / f.sum(0) - 0.5 * g
+    prof = ux[0, :, 0]
+    a = math.sqrt(2.0) * cs * cs
+    H = float(ny)
+
+    def dudy(y):
+        rhs = g * (H / 2 - y)
+        return (-nu0 + math.sqrt(nu0 * nu0 + 4 * a * rhs)) / (2 * a)
+
+    ys = np.linspace(0.0, H / 2, 4001)
+    du = np.array([dudy(v) for v in ys])
+    u = np.concatenate([[0.0], np.cumsum(0.5 * (du[1:] + du[:-1]) * np.diff(ys))])
+    ref = np.interp(np.minimum(np.arange(ny) + 0.5, H - (np.arange(ny) + 0.5)), ys, u)
+    lam = np.array([poiseuille(v, H, g, nu0) for v in np.arange(ny) + 0.5])
+    # the model slows the channel down substantially, and as the closure says
+    assert prof.max() < 0.8 * lam.max()
+    assert np.max(np.abs(prof - ref)) / ref.max() < 0.03
