@@ -218,6 +218,9 @@ def main():
                     help="steps for the FP64 comparison line (default: steps // 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=256,
+                    help="edge of the drop-impact cube (256 = the benchmark workload; smaller "
+                         "sizes scale pool and drop, for profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -250,7 +253,12 @@ def main():
     build.build()
     from paper_2207_14496_gb300 import fsl
 
-    w = inputs.drop_impact()
+    if args.size == 256:
+        w = inputs.drop_impact()
+    else:
+        f = args.size / 256.0
+        w = inputs.drop_impact(n=args.size, pool=int(round(96 * f)), diameter=40.0 * f,
+                               gap=30.0 * f)
     peaks = load_peaks()
     precs = [p for p in args.precisions.split(",") if p]
     res = {}
@@ -297,7 +305,7 @@ def main():
         e2e = dict(value=world * e["mlups"], unit="MLUPS",
                    h2d_bytes_per_step=e["h2d_per_step"], d2h_bytes_per_step=e["d2h_per_step"])
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.size == 256:
         cpu = cpu_baseline(w, steps=1)
     if rank == 0:
         clocks = h["clocks"]
@@ -306,7 +314,8 @@ def main():
             warmup=args.warmup, ms_per_step=ms_max / h["steps"], higher_is_better=True,
             scaling="weak", vs_baseline=None, dtype="f32" if head != "fp64" else "f64",
             storage=head, data="synthetic",
-            config=dict(workload=WORKLOAD, shape=[256, 256, 256], lattice="D3Q27",
+            config=dict(workload=WORKLOAD if args.size == 256 else f"drop_impact_{args.size}",
+                        shape=[args.size] * 3, lattice="D3Q27",
                         collision="TRT 3/16", refill="eq", sigma=1e-4, gravity=1e-6,
                         nu=round(inputs.DROP_NU, 9), parallelism=f"replicas{world}",
                         l2="inputs larger than L2 (PDF buffers >= 1.8 GB)"),

@@ -91,6 +91,9 @@ typedef struct {
   double p_volume;  /* volume (atmospheric) gas pressure, 1/3 for rho = 1 */
   double eps_phi;   /* conversion threshold epsilon_phi (1e-2 in the paper) */
   unsigned options; /* FSL_OPT_* */
+  double les_cs;    /* Smagorinsky constant C_S (Sec. 2.1, 0.1 in the paper's dam breaks);
+                       0 disables the turbulence model */
+  int free_slip[3]; /* per non-periodic axis: 1 = free-slip (specular) walls, 0 = no-slip */
 } fsl_config;
 
 /* Workspace size for a configuration.  bytes: out.  FSL_ERR_ARG for an
@@ -165,16 +168,51 @@ fsl_status fsl_lattice_table(int lattice, int* c3q, double* w);
 /* Number of kernel launches one fsl_step(1) issues. */
 int fsl_launches_per_step(const fsl_handle* h);
 
+/* Bulk stream-collide kernel of the FP32 / FP16 / BF16 storages (the FP64
+ * path has one kernel).  All variants collide two neighbouring cells at once
+ * in packed FP32 and give identical results (same explicitly rounded
+ * arithmetic on the same inputs); they differ in how the stored values reach
+ * the registers:
+ *   PAIR, PAIR_R128: two cells per thread, 128 threads per block (tiles of
+ *     256 cells along x), one aligned 2-value load per direction, values
+ *     pulled from x -/+ 1 exchanged between lanes by warp shuffles; PAIR lets
+ *     the compiler use as many registers as it likes, PAIR_R128 caps them at
+ *     128 (four blocks per SM);
+ *   PAIR64_R128: as PAIR_R128 with 64-thread blocks;
+ *   TMA: persistent, tiles of 256 cells with liquid (listed by a pre-pass)
+ *     staged in shared memory by bulk copies through a ring of
+ *     mbarrier-guarded stages, one producer warp and four consumer warps;
+ *   QUAD_64 (16-bit storages only): four cells per thread, 64 threads per
+ *     block, one 8-byte load per direction kept packed until the collision;
+ *   WARP_TMA: persistent, every warp streams its own 64-cell row segments
+ *     with liquid (listed by a pre-pass) through a private ring of
+ *     shared-memory stages filled by bulk copies, two cells per lane;
+ *   PAIR_PIPE (16-bit storages only): as PAIR_R128, but each block walks a
+ *     strided sequence of rows and issues the loads of its next row before
+ *     colliding the current one (software pipelining over rows).
+ * DEFAULT is PAIR_R128; the Python autotuner
+ * (paper_2207_14496_gb300.autotune) measures the variants instead.
+ * fsl_set_variant drops captured step graphs; FSL_ERR_ARG for an unknown
+ * variant and for QUAD_64 or PAIR_PIPE with FP32 storage. */
+enum { FSL_VARIANT_DEFAULT = 0, FSL_VARIANT_PAIR = 1, FSL_VARIANT_PAIR_R128 = 2,
+       FSL_VARIANT_PAIR64_R128 = 3, FSL_VARIANT_TMA = 4, FSL_VARIANT_QUAD_64 = 5,
+       FSL_VARIANT_WARP_TMA = 6, FSL_VARIANT_PAIR_PIPE = 7 };
+fsl_status fsl_set_variant(fsl_handle* h, int variant);
+int fsl_get_variant(const fsl_handle* h);
+
 /* Measurement of one kernel on the current state, for roofline reports.
  * kernel: FSL_KERNEL_STREAM_COLLIDE, the bulk pull stream-collide pass over
- * all cells (Eqs. nm-lbm-collision, nm-lbm-streaming; liquid cells).  Launches
- * it `reps` times on the bound stream, each bracketed by CUDA events, and
- * leaves the simulation state unchanged (the pass only reads the current PDF
- * buffer and writes the other one).  out4 (host, 4 doubles): average launch
- * time in ms, algorithmic bytes per launch (liquid cells x 2 q x storage bytes
- * + one flag byte per cell + 4 bytes per interface cell listed), number of
- * liquid cells, number of interface cells.  Synchronises the stream. */
-enum { FSL_KERNEL_STREAM_COLLIDE = 1 };
+ * all cells (Eqs. nm-lbm-collision, nm-lbm-streaming; liquid cells), timed
+ * alone; FSL_KERNEL_BULK_PASS, the same pass together with the list pre-pass
+ * that some variants launch before it (what one step spends on the bulk).
+ * Launches it `reps` times on the bound stream, each bracketed by CUDA
+ * events, and leaves the simulation state unchanged (the pass only reads the
+ * current PDF buffer and writes the other one).  out4 (host, 4 doubles):
+ * average launch time in ms, algorithmic bytes per launch (liquid cells x
+ * 2 q x storage bytes + one flag byte per cell + 4 bytes per interface cell
+ * listed), number of liquid cells, number of interface cells.  Synchronises
+ * the stream.  FSL_ERR_ARG for another kernel code or reps < 1. */
+enum { FSL_KERNEL_STREAM_COLLIDE = 1, FSL_KERNEL_BULK_PASS = 2 };
 fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4);
 
 /* Total mass of a state held in caller-owned device arrays, for callers that
@@ -199,6 +237,36 @@ fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4);
 fsl_status fsl_total_mass_noalloc(const fsl_config* cfg, const void* d_pdf,
                                   const unsigned char* d_types, const double* d_mass,
                                   const double* d_lost, double* d_out, void* cuda_stream);
+
+/* Batched stepping of many independent domains (the paper runs one domain at
+ * a time; this is the throughput form for sets of small problems of uneven
+ * sizes and refilling schemes).  A batch groups existing handles, each with
+ * its own configuration, workspace and state; fsl_batch_step advances every
+ * member by nsteps with one CUDA-graph launch per chunk of steps on the
+ * batch's stream.  Inside that graph each member's kernels form an
+ * independent branch (a child graph per member, no edges between members),
+ * so the GPU runs the domains side by side instead of one after another.
+ *   handles: host array of n >= 1 handles, all initialised (fsl_init_fill or
+ *     fsl_load done) and bound to streams of one device; the batch keeps the
+ *     pointers, not the array; the handles must outlive the batch;
+ *   cuda_stream: the stream the graphs launch on (cudaStream_t as void*, not
+ *     the legacy default stream);
+ *   chunk: steps per captured graph, 1..64 (each member contributes
+ *     chunk x fsl_launches_per_step kernel nodes to a graph);
+ *   out: receives the batch (release with fsl_batch_destroy, which leaves the
+ *     handles alone).
+ * fsl_batch_step orders itself after the work already queued on every
+ * member's stream and queues the members' later work after it, so
+ * fsl_observe on a member sees the batched steps.  A member that was
+ * re-initialised, loaded or given another variant since the last capture is
+ * recaptured.  Each member's results are bit-identical to fsl_step on it
+ * alone.  Errors: FSL_ERR_ARG (null, n < 1, chunk out of range, a null or
+ * uninitialised member), FSL_ERR_CUDA (capture, instantiation or launch). */
+typedef struct fsl_batch fsl_batch;
+fsl_status fsl_batch_create(fsl_handle* const* handles, int n, void* cuda_stream, int chunk,
+                            fsl_batch** out);
+fsl_status fsl_batch_step(fsl_batch* b, int nsteps);
+fsl_status fsl_batch_destroy(fsl_batch* b);
 
 /* Static description of a status code; last CUDA error text of this thread. */
 const char* fsl_status_string(fsl_status s);

@@ -32,7 +32,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 enum Region {
   R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST,
-  R_LIF, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_CTRL, R_TRACE, R_RED, R_COUNT
+  R_LIF, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_LTILES, R_CTRL, R_TRACE, R_RED, R_COUNT
 };
 
 bool valid_config(const fsl_config* c) {
@@ -48,6 +48,7 @@ bool valid_config(const fsl_config* c) {
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(c->gravity[a])) return false;
   if (!std::isfinite(c->sigma) || !std::isfinite(c->p_volume)) return false;
+  if (!(c->les_cs >= 0.0) || !std::isfinite(c->les_cs)) return false;
   const long long sx = ((long long)c->nx + 31) / 32 * 32;
   const long long cells = sx * c->ny * (long long)c->nz;
   const long long plane = (cells + 127) / 128 * 128;
@@ -65,6 +66,10 @@ void make_geom(const fsl_config* c, Geom* g) {
   g->plane = (g->cells + 127) / 128 * 128;
   for (int a = 0; a < 3; ++a) g->periodic[a] = c->periodic[a] ? 1 : 0;
   g->has_obst = 0;
+  g->variant = FSL_VARIANT_DEFAULT;
+  g->free_slip = 0;
+  for (int a = 0; a < 3; ++a)
+    if (c->free_slip[a] && !c->periodic[a]) g->free_slip |= 1 << a;
 }
 
 void make_phys(const fsl_config* c, Phys* p) {
@@ -93,6 +98,24 @@ void make_phys(const fsl_config* c, Phys* p) {
   p->geq_coef = (c->options & FSL_OPT_GEQ_LITERAL_NU) ? 1.5 / c->nu : 1.5 * p->tau;
   p->thr_hi = 1.0 + c->eps_phi;
   p->thr_lo = 0.0 - c->eps_phi;
+  p->magic = c->trt_magic;
+  p->les_cs = c->les_cs;
+  p->f.tau = (float)p->tau;
+  p->f.omega = (float)p->omega;
+  p->f.lam_e = (float)p->lam_e;
+  p->f.lam_o = (float)p->lam_o;
+  p->f.pre_e = (float)p->pre_e;
+  p->f.pre_o = (float)p->pre_o;
+  for (int a = 0; a < 3; ++a) p->f.g[a] = (float)p->g[a];
+  p->f.sigma = (float)p->sigma;
+  p->f.p_v = (float)p->p_v;
+  p->f.eps = (float)p->eps;
+  p->f.geq_coef = (float)p->geq_coef;
+  p->f.thr_hi = (float)p->thr_hi;
+  p->f.thr_lo = (float)p->thr_lo;
+  p->f.magic = (float)p->magic;
+  p->f.les_cs = (float)p->les_cs;
+  p->f.les_k = (float)(2.0 * std::sqrt(2.0) * p->les_cs * p->les_cs * 9.0);
 }
 
 void region_sizes(const fsl_config* c, const Geom& g, size_t* sz) {
@@ -103,6 +126,8 @@ void region_sizes(const fsl_config* c, const Geom& g, size_t* sz) {
   sz[R_PHI] = sz[R_PHINEW] = sz[R_MASS] = sz[R_RHO] = sz[R_KAPPA] = sz[R_MEX] = sz[R_LOST] =
       cells * sizeof(double);
   for (int r = R_LIF; r <= R_LRECV; ++r) sz[r] = cells * sizeof(int);
+  // tile lists of the shared-memory variants: up to one entry per 64 cells of a row
+  sz[R_LTILES] = (size_t)((g.nx + 63) / 64) * g.ny * g.nz * sizeof(int);
   sz[R_CTRL] = sizeof(Ctrl);
   sz[R_TRACE] = (size_t)kTraceCapacity * 3 * sizeof(double);
   sz[R_RED] = (size_t)(2 * kReduceBlocks + 16) * sizeof(double);
@@ -210,6 +235,7 @@ struct fsl_handle {
   bool ready;
   int trace_every;
   std::map<int, cudaGraphExec_t> graphs;
+  unsigned gen = 0;  // bumped whenever captured launch parameters may change
 };
 
 namespace {
@@ -281,6 +307,7 @@ fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, vo
   d.l_new = reinterpret_cast<int*>(base + h->off[R_LNEW]);
   d.l_l2i = reinterpret_cast<int*>(base + h->off[R_LL2I]);
   d.l_recv = reinterpret_cast<int*>(base + h->off[R_LRECV]);
+  d.l_tiles = reinterpret_cast<int*>(base + h->off[R_LTILES]);
   d.ctrl = reinterpret_cast<Ctrl*>(base + h->off[R_CTRL]);
   d.trace = reinterpret_cast<double*>(base + h->off[R_TRACE]);
   d.red = reinterpret_cast<double*>(base + h->off[R_RED]);
@@ -315,6 +342,7 @@ fsl_status fsl_init_fill(fsl_handle* h, const double* phi, const double* u0,
       if (obstacle[k]) { h->g.has_obst = 1; break; }
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
+  ++h->gen;
   FSL_CK(h->L->init(h->d, h->g, h->p, 0, su, obstacle ? 1 : 0, h_ref, h->stream));
   k_set_trace<<<1, 32, 0, h->stream>>>(h->d.ctrl, h->trace_every);
   FSL_CK(cudaGetLastError());
@@ -544,13 +572,14 @@ fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
         }
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
+  ++h->gen;
   for (auto& pr : parts) {
     FSL_CK(cudaMemcpyAsync(pr.first, s, pr.second, cudaMemcpyHostToDevice, h->stream));
     s += pr.second;
   }
   // per-step scratch restarts empty: counters zero, claim bytes zero
   c.n_if = c.n_fill = c.n_empty = c.n_new = c.n_l2i = c.n_recv = 0;
-  c.pad[0] = 0;
+  c.n_emptied = c.end_blocks = c.n_tiles = 0;
   c.trace_every = h->trace_every;
   c.trace_count = 0;
   FSL_CK(cudaMemcpyAsync(h->d.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
@@ -567,6 +596,132 @@ fsl_status fsl_destroy(fsl_handle* h) {
   return FSL_OK;
 }
 
+// ------------------------------------------------------------------ batch
+struct fsl_batch {
+  std::vector<fsl_handle*> hs;
+  cudaStream_t stream = nullptr;  // graph launches
+  cudaStream_t cap = nullptr;     // private stream, used only for captures
+  std::vector<cudaEvent_t> ev;    // per member: its stream's queued work
+  cudaEvent_t done = nullptr;
+  int chunk = 8;
+  std::vector<unsigned> gens;     // member generations the graphs were captured at
+  std::map<int, cudaGraphExec_t> graphs;
+};
+
+namespace {
+
+void batch_drop_graphs(fsl_batch* b) {
+  for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  b->graphs.clear();
+}
+
+// one graph of `steps` steps of every member: a child graph per member, no
+// edges between them
+fsl_status batch_capture(fsl_batch* b, int steps, cudaGraphExec_t* out) {
+  cudaGraph_t parent;
+  FSL_CK(cudaGraphCreate(&parent, 0));
+  for (fsl_handle* h : b->hs) {
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(parent);
+      return cuda_fail(e, "cudaStreamBeginCapture (batch)");
+    }
+    cudaError_t le = cudaSuccess;
+    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = h->L->step(h->d, h->g, h->p, b->cap);
+    e = cudaStreamEndCapture(b->cap, &g);
+    if (le != cudaSuccess || e != cudaSuccess) {
+      if (e == cudaSuccess) cudaGraphDestroy(g);
+      cudaGraphDestroy(parent);
+      return cuda_fail(le != cudaSuccess ? le : e, "batch member capture");
+    }
+    cudaGraphNode_t node;
+    e = cudaGraphAddChildGraphNode(&node, parent, nullptr, 0, g);
+    cudaGraphDestroy(g);  // the child node holds its own copy
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(parent);
+      return cuda_fail(e, "cudaGraphAddChildGraphNode");
+    }
+  }
+  cudaError_t ie = cudaGraphInstantiate(out, parent, 0);
+  cudaGraphDestroy(parent);
+  if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate (batch)");
+  return FSL_OK;
+}
+
+}  // namespace
+
+fsl_status fsl_batch_create(fsl_handle* const* handles, int n, void* cuda_stream, int chunk,
+                            fsl_batch** out) {
+  if (!handles || n < 1 || !out || !cuda_stream || chunk < 1 || chunk > (int)kGraphChunk)
+    return FSL_ERR_ARG;
+  for (int i = 0; i < n; ++i)
+    if (!handles[i] || !handles[i]->ready) return FSL_ERR_ARG;
+  fsl_batch* b = new fsl_batch;
+  b->hs.assign(handles, handles + n);
+  b->stream = (cudaStream_t)cuda_stream;
+  b->chunk = chunk;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  b->ev.assign(n, nullptr);
+  for (int i = 0; i < n && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&b->ev[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    fsl_batch_destroy(b);
+    return cuda_fail(e, "batch streams/events");
+  }
+  *out = b;
+  return FSL_OK;
+}
+
+fsl_status fsl_batch_step(fsl_batch* b, int nsteps) {
+  if (!b || nsteps < 0) return FSL_ERR_ARG;
+  if (nsteps == 0) return FSL_OK;
+  const size_t n = b->hs.size();
+  bool stale = b->gens.size() != n;
+  for (size_t i = 0; i < n && !stale; ++i) stale = b->gens[i] != b->hs[i]->gen;
+  if (stale) {
+    for (fsl_handle* h : b->hs)
+      if (!h->ready) return FSL_ERR_STATE;
+    batch_drop_graphs(b);
+    b->gens.resize(n);
+    for (size_t i = 0; i < n; ++i) b->gens[i] = b->hs[i]->gen;
+  }
+  // after everything already queued on the members' streams
+  for (size_t i = 0; i < n; ++i) {
+    FSL_CK(cudaEventRecord(b->ev[i], b->hs[i]->stream));
+    FSL_CK(cudaStreamWaitEvent(b->stream, b->ev[i], 0));
+  }
+  int left = nsteps;
+  while (left > 0) {
+    const int c = left >= b->chunk ? b->chunk : left;
+    auto it = b->graphs.find(c);
+    if (it == b->graphs.end()) {
+      cudaGraphExec_t exec;
+      fsl_status st = batch_capture(b, c, &exec);
+      if (st != FSL_OK) return st;
+      it = b->graphs.emplace(c, exec).first;
+    }
+    FSL_CK(cudaGraphLaunch(it->second, b->stream));
+    left -= c;
+  }
+  // members' later work after the batched steps
+  FSL_CK(cudaEventRecord(b->done, b->stream));
+  for (fsl_handle* h : b->hs) FSL_CK(cudaStreamWaitEvent(h->stream, b->done, 0));
+  return FSL_OK;
+}
+
+fsl_status fsl_batch_destroy(fsl_batch* b) {
+  if (!b) return FSL_ERR_ARG;
+  batch_drop_graphs(b);
+  for (cudaEvent_t e : b->ev)
+    if (e) cudaEventDestroy(e);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+  return FSL_OK;
+}
+
 fsl_status fsl_lattice_table(int lattice, int* c3q, double* w) {
   if (lattice != FSL_D3Q19 && lattice != FSL_D3Q27) return FSL_ERR_ARG;
   for (int i = 0; i < lattice; ++i) {
@@ -577,11 +732,28 @@ fsl_status fsl_lattice_table(int lattice, int* c3q, double* w) {
   return FSL_OK;
 }
 
-int fsl_launches_per_step(const fsl_handle* h) { return h ? h->L->launches_per_step : 0; }
+int fsl_launches_per_step(const fsl_handle* h) { return h ? h->L->launches_per_step(h->g) : 0; }
+
+fsl_status fsl_set_variant(fsl_handle* h, int variant) {
+  if (!h || variant < FSL_VARIANT_DEFAULT || variant > FSL_VARIANT_PAIR_PIPE) return FSL_ERR_ARG;
+  if ((variant == FSL_VARIANT_QUAD_64 || variant == FSL_VARIANT_PAIR_PIPE) &&
+      storage_bytes(h->cfg.precision) != 2)
+    return FSL_ERR_ARG;
+  h->g.variant = variant;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  ++h->gen;
+  return FSL_OK;
+}
+
+int fsl_get_variant(const fsl_handle* h) { return h ? h->g.variant : -1; }
 
 fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
-  if (!h || !out4 || reps < 1 || kernel != FSL_KERNEL_STREAM_COLLIDE) return FSL_ERR_ARG;
+  if (!h || !out4 || reps < 1 ||
+      (kernel != FSL_KERNEL_STREAM_COLLIDE && kernel != FSL_KERNEL_BULK_PASS))
+    return FSL_ERR_ARG;
   if (!h->ready) return FSL_ERR_STATE;
+  const bool with_pre = kernel == FSL_KERNEL_BULK_PASS;
   unsigned long long* cnt = reinterpret_cast<unsigned long long*>(h->d.red + 2 * kReduceBlocks + 8);
   FSL_CK(cudaMemsetAsync(cnt, 0, 2 * sizeof(unsigned long long), h->stream));
   k_count_types<<<kReduceBlocks, 256, 0, h->stream>>>(h->d, h->g, cnt);
@@ -593,9 +765,20 @@ fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
   FSL_CK(cudaEventCreate(&e1));
   double total_ms = 0.0;
   cudaError_t err = cudaSuccess;
+  // work lists of the current state (interface cells, liquid tiles), untimed
+  // unless the pre-pass is part of what is measured
+  if (!with_pre) {
+    err = cudaMemsetAsync(&h->d.ctrl->n_tiles, 0, sizeof(unsigned), h->stream);
+    if (err == cudaSuccess) err = h->L->pre_bulk(h->d, h->g, h->p, h->stream);
+  }
   for (int r = 0; r < reps && err == cudaSuccess; ++r) {
-    err = cudaMemsetAsync(&h->d.ctrl->n_if, 0, sizeof(unsigned), h->stream);
+    // the lists are rebuilt by whichever kernel builds them in a step
+    if (with_pre || h->L->launches_per_step(h->g) == 11)
+      err = cudaMemsetAsync(&h->d.ctrl->n_if, 0, sizeof(unsigned), h->stream);
+    if (err == cudaSuccess && with_pre)
+      err = cudaMemsetAsync(&h->d.ctrl->n_tiles, 0, sizeof(unsigned), h->stream);
     if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
+    if (err == cudaSuccess && with_pre) err = h->L->pre_bulk(h->d, h->g, h->p, h->stream);
     if (err == cudaSuccess) err = h->L->stream_collide(h->d, h->g, h->p, h->stream);
     if (err == cudaSuccess) err = cudaEventRecord(e1, h->stream);
     if (err == cudaSuccess) err = cudaEventSynchronize(e1);
@@ -604,6 +787,7 @@ fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
     total_ms += ms;
   }
   if (err == cudaSuccess) err = cudaMemsetAsync(&h->d.ctrl->n_if, 0, sizeof(unsigned), h->stream);
+  if (err == cudaSuccess) err = cudaMemsetAsync(&h->d.ctrl->n_tiles, 0, sizeof(unsigned), h->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -1,0 +1,477 @@
+// Bulk pass of the 16/32-bit path, staged through shared memory by the TMA.
+//
+// k_tiles lists, at the start of a step, the tiles (256 cells along x of one
+// (y, z) row) that hold liquid cells, and compacts the interface cells of
+// every tile into the interface list (warp ballots).
+//
+// k_stream_collide_bulk is persistent and warp-specialised.  Its producer warp
+// walks the CTA's share of the tile list and, for each tile, issues Q + 1
+// one-dimensional bulk copies (cp.async.bulk, the untiled TMA form) into a
+// ring of shared-memory stages: for each direction i the 256 + 2*8 stored
+// values of plane i on the row (y - c_iy, z - c_iz) that the tile pulls
+// from (clipped to the row), and the tile's 256 flag bytes.  Each copy group
+// completes on the stage's "full" mbarrier.  Four consumer warps, two
+// neighbouring cells per thread, wait on "full", pull their 27 (or 19) value
+// pairs out of shared memory, collide both cells in packed FP32 (collide_v)
+// and store the result to HBM, then release the stage through its "empty"
+// mbarrier so that the producer can refill it.  With
+// several stages in flight per CTA the HBM traffic does not wait on the
+// collision arithmetic.
+//
+// Alignment: every copy starts at an element index that is a multiple of 8
+// (tile starts are multiples of 256, the halo is 8, rows are padded to 32),
+// so addresses and byte counts are multiples of 16.  Every mbarrier wait is
+// bounded; a wait that gives up latches bit 4 of the control block's error
+// word, stops the CTA's loops, and the producer waits (bounded) for the copies
+// it issued before the CTA exits.
+#pragma once
+// Included by fsl_kernels.cuh after collide_lp, pull_liquid and warp_append.
+
+namespace fsl {
+
+constexpr int kBulkTX = 256;    // cells per tile along x
+constexpr int kBulkHalo = 8;    // staged halo on each side (keeps copies 16-byte aligned)
+constexpr int kBulkSeg = kBulkTX + 2 * kBulkHalo;
+constexpr int kBulkConsumers = 4;                      // warps, two cells per thread
+constexpr int kBulkThreads = 32 * (kBulkConsumers + 1);  // + one producer warp
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase with the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  for (int it = 0; it < (1 << 20); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// ring depth and shared-memory layout per storage type
+template <int Q, class ST>
+struct BulkRing {
+  static constexpr int stages = sizeof(typename ST::T) == 2 ? 4 : 3;
+  static constexpr size_t pdf_bytes = (size_t)Q * kBulkSeg * sizeof(typename ST::T);
+  static constexpr size_t stage_bytes = pdf_bytes + kBulkTX;  // + flag bytes
+  // stages, then full[stages] and empty[stages] barriers, the tile index of
+  // each stage and the abort flag
+  static constexpr size_t bytes = stages * stage_bytes + 2 * stages * 8 + 4 * stages + 16;
+};
+
+// List the tiles (TX cells along x of one row) with liquid cells; compact the
+// interface cells.  One warp per tile, TX / 32 consecutive cells per lane.
+template <int TX>
+__global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
+  constexpr int CPL = TX / 32;
+  static_assert(CPL == 2 || CPL == 8, "tiles of 64 or 256 cells");
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const long long ntiles = (long long)ntx * g.ny * g.nz;
+  const long long k = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (k >= ntiles) return;  // whole warp
+  const int lane = threadIdx.x & 31;
+  const int x0 = (int)(k % ntx) * TX;
+  const long long row = k / ntx;
+  const int xl = x0 + CPL * lane;
+  uint2 f8 = make_uint2(0u, 0u);
+  if (xl < g.sx) {
+    if constexpr (CPL == 8) {
+      f8 = *reinterpret_cast<const uint2*>(d.flags + row * g.sx + xl);
+    } else {
+      const uchar2 b2 = *reinterpret_cast<const uchar2*>(d.flags + row * g.sx + xl);
+      f8.x = (unsigned)b2.x | ((unsigned)b2.y << 8);
+    }
+  }
+  bool liq = false;
+  unsigned m[CPL];
+  unsigned total = 0;
+#pragma unroll
+  for (int b = 0; b < CPL; ++b) {
+    const unsigned byte = ((b < 4 ? f8.x : f8.y) >> (8 * (b & 3))) & 0xffu;
+    const bool in = xl + b < g.nx;
+    const int t = in ? (int)(byte & F_TYPE) : T_GAS;
+    liq |= t == T_LIQ;
+    m[b] = __ballot_sync(0xffffffffu, t == T_IF);
+    total += __popc(m[b]);
+  }
+  // one list reservation per warp for its interface cells
+  if (total) {
+    unsigned base = 0;
+    if (lane == 0) base = atomicAdd(&ctrl->n_if, total);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    const unsigned below = (1u << lane) - 1u;
+    // list order: cell by cell within the lane's run, lanes in order
+#pragma unroll
+    for (int b = 0; b < CPL; ++b) {
+      if ((m[b] >> lane) & 1u) d.l_if[base + __popc(m[b] & below)] = (int)(row * g.sx + xl + b);
+      base += __popc(m[b]);
+    }
+  }
+  if (__any_sync(0xffffffffu, liq) && lane == 0) d.l_tiles[atomicAdd(&ctrl->n_tiles, 1u)] = (int)k;
+}
+
+// Update of two neighbouring cells (xa, xa + 1) whose pulled values sit in a
+// staged row segment: stage holds, per direction i, the stored values of
+// plane i on the source row (y - c_iy, z - c_iz) from x = x0 - halo on, `seg`
+// values per direction; li is the staged index of cell xa.  Values are read
+// out of shared memory, both cells collide in packed FP32 and the results go
+// to HBM.  The periodic wrap along x at the two row ends and liquid cells next
+// to a wall or obstacle (per-direction path) read HBM instead.  Returns
+// whether a liquid cell reached |u|^2 >= 1/3.
+template <int Q, class ST>
+__device__ __forceinline__ bool bulk_pair(const typename ST::T* stage, int seg, int li, int xa,
+                                          int row, uint8_t fl0, uint8_t fl1, const Dev& d,
+                                          const Geom& g, const Phys& p, const LesLp& les) {
+  using T = typename ST::T;
+  constexpr float S = ST::kScaleF;
+  const bool liq0 = (fl0 & F_TYPE) == T_LIQ, liq1 = (fl1 & F_TYPE) == T_LIQ;
+  if (!liq0 && !liq1) return false;
+  const int cur = d.ctrl->step & 1;
+  const T* __restrict__ A = (const T*)d.pdf[cur];
+  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
+  const long long P = g.plane;
+  float2 f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = dir_c(i, 0);
+    if constexpr (sizeof(T) == 2) {
+      const unsigned short* sg = reinterpret_cast<const unsigned short*>(stage) + (size_t)i * seg;
+      unsigned wv;
+      if (cx == 0) {
+        wv = *reinterpret_cast<const unsigned*>(sg + li);
+      } else {  // (li - cx, li + 1 - cx) straddles a 32-bit word
+        wv = (unsigned)sg[li - cx] | ((unsigned)sg[li + 1 - cx] << 16);
+      }
+      f[i] = ST::unpack2(wv);
+    } else {
+      const T* sg = stage + (size_t)i * seg;
+      f[i] = make_float2(ST::ld1s(sg + li - cx), ST::ld1s(sg + li + 1 - cx));
+    }
+  }
+  const int y = row % g.ny, z = row / g.ny;
+  if (g.periodic[0] && (xa == 0 || xa + 1 >= g.nx - 1)) {
+    // periodic wrap along x: the value comes from the other end of the row
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = dir_c(i, 0);
+      if (cx == 0) continue;
+      const T* src = A + i * P +
+                     (long long)g.sx * (((y - dir_c(i, 1) + g.ny) % g.ny) +
+                                        g.ny * ((z - dir_c(i, 2) + g.nz) % g.nz));
+      if (cx == 1 && xa == 0) f[i].x = ST::ld1(src + g.nx - 1);
+      if (cx == -1 && xa == g.nx - 1) f[i].x = ST::ld1(src);
+      if (cx == -1 && xa + 1 == g.nx - 1) f[i].y = ST::ld1(src);
+    }
+  }
+  const long long c = (long long)row * g.sx + xa;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint8_t fh = h ? fl1 : fl0;
+    if ((fh & F_TYPE) == T_LIQ && (fh & F_NEAR_OBST)) {
+      float tv[Q];
+      Nbr nb;
+      nb.setup(g, xa + h, y, z);
+      pull_liquid<Q, ST>(A, P, d.flags, nb, (int)c + h, true, tv);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) Lanes<float2>::at(f[i], h) = tv[i] * S;
+    }
+  }
+  const bool tr = p.trt != 0;
+  const float lamE = p.f.lam_e, lamO = tr ? p.f.lam_o : p.f.omega;
+  const float pe = p.f.pre_e, po = tr ? p.f.pre_o : p.f.pre_e;
+  const float2 usq = collide_v<Q, float2>(f, f, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2],
+                                          S, les);
+  T* out = B + c;
+  if (liq0 && liq1) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st2(out + i * P, f[i].x, f[i].y);
+  } else if (liq0) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st1(out + i * P, f[i].x);
+  } else {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st1(out + i * P + 1, f[i].y);
+  }
+  return (liq0 && !(usq.x < (float)(1.0 / 3.0))) || (liq1 && !(usq.y < (float)(1.0 / 3.0)));
+}
+
+template <int Q, class ST>
+__global__ void __launch_bounds__(kBulkThreads, 2)
+    k_stream_collide_bulk(Dev d, Geom g, Phys p, int ntx) {
+  using T = typename ST::T;
+  using RING = BulkRing<Q, ST>;
+  constexpr int D = RING::stages;
+  constexpr float S = ST::kScaleF;
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + D * RING::stage_bytes);
+  uint64_t* empty = full + D;
+  int* tile_of = reinterpret_cast<int*>(empty + D);  // tile index held by each stage
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tile_of + D);
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int cur = ctrl->step & 1;
+  const T* __restrict__ A = (const T*)d.pdf[cur];
+  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
+  const long long P = g.plane;
+  const int ntl = (int)ctrl->n_tiles;
+  if ((int)blockIdx.x >= ntl) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < D; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kBulkConsumers);
+    }
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  __syncthreads();
+
+  if (warp == kBulkConsumers) {
+    // ---------------- producer warp: lane 0 waits for the stage and arms its
+    // barrier, lane i < Q copies direction i, lane Q the flags
+    int issued = 0;
+    bool stop = false;
+    for (int j = 0;; ++j) {
+      const int ti = blockIdx.x + j * gridDim.x;
+      if (ti >= ntl) break;
+      const int s = j % D;
+      int go = 1;
+      if (lane == 0) {
+        if (j >= D && !mbar_wait(&empty[s], ((j / D) - 1) & 1)) {
+          *abort_flag = 1;
+          atomicOr(&ctrl->timeout, 4u);
+        }
+        go = *abort_flag == 0;
+      }
+      if (!__shfl_sync(0xffffffffu, go, 0)) {
+        stop = true;
+        break;
+      }
+      const int k = d.l_tiles[ti];
+      const int x0 = (k % ntx) * kBulkTX;
+      const int row = k / ntx;
+      const int lo = x0 - kBulkHalo > 0 ? x0 - kBulkHalo : 0;
+      const int hi = x0 + kBulkTX + kBulkHalo < g.sx ? x0 + kBulkTX + kBulkHalo : g.sx;
+      const unsigned bytes = (unsigned)((hi - lo) * sizeof(T));
+      const unsigned fbytes = (unsigned)(g.sx - x0 < kBulkTX ? g.sx - x0 : kBulkTX);
+      unsigned char* stage = smem + (size_t)s * RING::stage_bytes;
+      if (lane == 0) {
+        tile_of[s] = k;  // published to the consumers by the arrive below
+        mbar_expect_tx(&full[s], bytes * Q + fbytes);
+      }
+      __syncwarp();
+      if (lane < Q) {
+        const int i = lane;
+        const int y = row % g.ny, z = row / g.ny;
+        const int cy = rc(i, 1), cz = rc(i, 2);
+        int ys = y - cy, zs = z - cz;
+        ys = ys < 0 ? (g.periodic[1] ? g.ny - 1 : y) : (ys >= g.ny ? (g.periodic[1] ? 0 : y) : ys);
+        zs = zs < 0 ? (g.periodic[2] ? g.nz - 1 : z) : (zs >= g.nz ? (g.periodic[2] ? 0 : z) : zs);
+        const T* src = A + i * P + (long long)g.sx * (ys + g.ny * zs) + lo;
+        T* dst = reinterpret_cast<T*>(stage) + (lo - (x0 - kBulkHalo)) + (size_t)i * kBulkSeg;
+        bulk_copy_g2s(dst, src, bytes, &full[s]);
+      } else if (lane == Q) {
+        bulk_copy_g2s(stage + RING::pdf_bytes, d.flags + (long long)row * g.sx + x0, fbytes,
+                      &full[s]);
+      }
+      ++issued;
+    }
+    if (stop && lane == 0) {
+      // let the copies this CTA issued land before its shared memory goes away
+      const int first = issued > D ? issued - D : 0;
+      for (int j = first; j < issued; ++j) mbar_wait(&full[j % D], (j / D) & 1);
+    }
+    return;
+  }
+
+  // ---------------- consumer warps: two cells (2t, 2t + 1) of the tile per thread
+  const LesLp les = LesLp::of(p);
+  const int t = threadIdx.x;
+  bool bad = false;
+  for (int j = 0;; ++j) {
+    const int ti = blockIdx.x + j * gridDim.x;
+    if (ti >= ntl) break;
+    const int s = j % D;
+    const bool ok = mbar_wait(&full[s], (j / D) & 1);
+    // the decision to stop is taken by the whole warp
+    if (__any_sync(0xffffffffu, !ok || *abort_flag != 0)) {
+      if (lane == 0) {
+        *abort_flag = 1;
+        atomicOr(&ctrl->timeout, 4u);
+      }
+      break;
+    }
+    const unsigned char* stage = smem + (size_t)s * RING::stage_bytes;
+    const int k = tile_of[s];
+    const int x0 = (k % ntx) * kBulkTX;
+    const int row = k / ntx;
+    const int xa = x0 + 2 * t;
+    const uchar2 f2 = *reinterpret_cast<const uchar2*>(stage + RING::pdf_bytes + 2 * t);
+    const uint8_t fl0 = xa < g.nx ? f2.x : (uint8_t)T_GAS;
+    const uint8_t fl1 = xa + 1 < g.nx ? f2.y : (uint8_t)T_GAS;
+    bad |= bulk_pair<Q, ST>(reinterpret_cast<const T*>(stage), kBulkSeg, kBulkHalo + 2 * t, xa, row,
+                            fl0, fl1, d, g, p, les);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
+// ------------------------------------------------------------------------
+// Per-warp TMA pipeline.  Every warp owns a ring of shared-memory stages and
+// streams its own sequence of 64-cell row segments (listed by k_tiles<64>):
+// lane 0 issues the Q + 1 bulk copies of segment j + D - 1 (per direction the
+// 64 + 2*8 stored values of the source row, and the 64 flag bytes) while the
+// whole warp updates segment j out of its stage, two cells per lane.  No
+// barrier spans more than one warp, so a slow warp holds up nobody, and the
+// loads in flight occupy shared memory instead of registers.  The stage a
+// warp has just read is handed back to the async proxy by a proxy fence
+// before lane 0 refills it.  Waits are bounded as in the block-level kernel.
+constexpr int kWarpTX = 64;
+constexpr int kWarpSeg = kWarpTX + 2 * kBulkHalo;
+constexpr int kWarpsPerBlock = 4;
+
+template <int Q, class ST>
+struct WarpRing {
+  static constexpr bool half = sizeof(typename ST::T) == 2;
+  static constexpr int stages = half ? 4 : 3;
+  static constexpr int min_blocks = half ? 3 : 2;  // blocks per SM the ring allows
+  static constexpr size_t pdf_bytes = (size_t)Q * kWarpSeg * sizeof(typename ST::T);
+  static constexpr size_t stage_bytes = (pdf_bytes + kWarpTX + 15) / 16 * 16;
+  // per warp: stages, then the full barriers and the segment index of each stage
+  static constexpr size_t tail_bytes = (stages * 8 + stages * 4 + 15) / 16 * 16;
+  static constexpr size_t warp_bytes = stages * stage_bytes + tail_bytes;
+  static constexpr size_t bytes = kWarpsPerBlock * warp_bytes;
+};
+
+template <int Q, class ST>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, WarpRing<Q, ST>::min_blocks)
+    k_stream_collide_wtma(Dev d, Geom g, Phys p, int ntx) {
+  using T = typename ST::T;
+  using RING = WarpRing<Q, ST>;
+  constexpr int D = RING::stages;
+  extern __shared__ __align__(128) unsigned char smem[];
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int ntl = (int)ctrl->n_tiles;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * kWarpsPerBlock + warp, tw = gridDim.x * kWarpsPerBlock;
+  if (gw >= ntl) return;  // whole warp; nothing below synchronises the block
+  unsigned char* ring = smem + (size_t)warp * RING::warp_bytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(ring + D * RING::stage_bytes);
+  int* seg_of = reinterpret_cast<int*>(full + D);
+  if (lane == 0) {
+    for (int s = 0; s < D; ++s) mbar_init(&full[s], 1);
+    mbar_fence_init();
+  }
+  __syncwarp();
+  const T* __restrict__ A = (const T*)d.pdf[ctrl->step & 1];
+  const long long P = g.plane;
+  // copies of the warp's jl-th segment into stage jl % D: lane 0 arms the
+  // stage's barrier, then lane i < Q issues direction i and lane Q the flags
+  // (warp-uniform call)
+  auto issue = [&](int jl) {
+    const int u = gw + jl * tw;
+    if (u >= ntl) return;
+    const int s = jl % D;
+    const int k = d.l_tiles[u];
+    const int x0 = (k % ntx) * kWarpTX;
+    const int row = k / ntx;
+    const int lo = x0 - kBulkHalo > 0 ? x0 - kBulkHalo : 0;
+    const int hi = x0 + kWarpTX + kBulkHalo < g.sx ? x0 + kWarpTX + kBulkHalo : g.sx;
+    const unsigned bytes = (unsigned)((hi - lo) * sizeof(T));
+    const unsigned fbytes = (unsigned)(g.sx - x0 < kWarpTX ? g.sx - x0 : kWarpTX);
+    unsigned char* stage = ring + (size_t)s * RING::stage_bytes;
+    if (lane == 0) {
+      seg_of[s] = k;  // published to the warp by the arrive below
+      mbar_expect_tx(&full[s], bytes * Q + fbytes);
+    }
+    __syncwarp();
+    if (lane < Q) {
+      const int i = lane;
+      const int y = row % g.ny, z = row / g.ny;
+      const int cy = rc(i, 1), cz = rc(i, 2);
+      int ys = y - cy, zs = z - cz;
+      ys = ys < 0 ? (g.periodic[1] ? g.ny - 1 : y) : (ys >= g.ny ? (g.periodic[1] ? 0 : y) : ys);
+      zs = zs < 0 ? (g.periodic[2] ? g.nz - 1 : z) : (zs >= g.nz ? (g.periodic[2] ? 0 : z) : zs);
+      const T* src = A + i * P + (long long)g.sx * (ys + g.ny * zs) + lo;
+      T* dst = reinterpret_cast<T*>(stage) + (lo - (x0 - kBulkHalo)) + (size_t)i * kWarpSeg;
+      bulk_copy_g2s(dst, src, bytes, &full[s]);
+    } else if (lane == Q) {
+      bulk_copy_g2s(stage + RING::pdf_bytes, d.flags + (long long)row * g.sx + x0, fbytes, &full[s]);
+    }
+  };
+  for (int jl = 0; jl < D - 1; ++jl) issue(jl);
+  const LesLp les = LesLp::of(p);
+  bool bad = false;
+  int done = 0;  // segments consumed
+  bool abort = false;
+  for (int jl = 0;; ++jl) {
+    const int u = gw + jl * tw;
+    if (u >= ntl) break;
+    const int s = jl % D;
+    issue(jl + D - 1);  // into the stage released last iteration
+    const bool ok = mbar_wait(&full[s], (jl / D) & 1);
+    if (__any_sync(0xffffffffu, !ok)) {
+      if (lane == 0) atomicOr(&ctrl->timeout, 4u);
+      abort = true;
+      break;
+    }
+    const unsigned char* stage = ring + (size_t)s * RING::stage_bytes;
+    const int k = seg_of[s];
+    const int x0 = (k % ntx) * kWarpTX;
+    const int row = k / ntx;
+    const int xa = x0 + 2 * lane;
+    const uchar2 f2 = *reinterpret_cast<const uchar2*>(stage + RING::pdf_bytes + 2 * lane);
+    const uint8_t fl0 = xa < g.nx ? f2.x : (uint8_t)T_GAS;
+    const uint8_t fl1 = xa + 1 < g.nx ? f2.y : (uint8_t)T_GAS;
+    bad |= bulk_pair<Q, ST>(reinterpret_cast<const T*>(stage), kWarpSeg, kBulkHalo + 2 * lane, xa,
+                            row, fl0, fl1, d, g, p, les);
+    // this lane's reads of the stage are complete before the refill
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncwarp();
+    done = jl + 1;
+  }
+  if (abort && lane == 0) {
+    // let every copy this warp issued land before its shared memory goes away
+    for (int jl = done; jl < done + D; ++jl) {
+      if (gw + jl * tw >= ntl) break;
+      mbar_wait(&full[jl % D], (jl / D) & 1);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
+}  // namespace fsl

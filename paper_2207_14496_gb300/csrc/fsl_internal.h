@@ -34,8 +34,10 @@ struct Ctrl {
   unsigned last[4];    // previous step: filled, emptied (after conflicts), new, interface
   int trace_every;     // 0: no trace
   int trace_count;     // records written (ring index = count % capacity)
-  unsigned timeout;    // bounded-wait error flag (never set by the step kernels)
-  unsigned pad[3];
+  unsigned timeout;    // error bits: 1 CAS retry cap, 2 refill without source, 4 copy wait gave up
+  unsigned n_emptied;  // to-gas cells actually converted this step
+  unsigned end_blocks; // end-of-step blocks finished
+  unsigned n_tiles;    // tiles holding liquid cells, listed this step (16/32-bit path)
 };
 
 constexpr int kTraceCapacity = 1 << 16;
@@ -49,6 +51,8 @@ struct Geom {
   long long plane;     // PDF plane stride in elements (>= cells, 128-element multiple)
   int periodic[3];
   int has_obst;        // the initial state had interior obstacle cells
+  int free_slip;       // bit a: the walls of non-periodic axis a are free-slip (specular)
+  int variant;         // bulk kernel of the 16/32-bit path (FSL_VARIANT_*; 0 = default)
 };
 
 struct Phys {
@@ -63,6 +67,15 @@ struct Phys {
   double sigma, p_v, eps;
   double geq_coef;                  // 1/(2 c_s^2 omega) = 1.5 tau, or 1.5/nu
   double thr_hi, thr_lo;            // 1 + eps, 0 - eps
+  double magic;                     // TRT magic parameter
+  double les_cs;                    // Smagorinsky constant, 0 = no turbulence model
+  // the same parameters rounded once to FP32 on the host, so that the 16/32-bit
+  // kernels execute no FP64 conversion (GB300 has two FP64 lanes per SM)
+  struct {
+    float tau, omega, lam_e, lam_o, pre_e, pre_o, g[3], sigma, p_v, eps, geq_coef, thr_hi,
+        thr_lo, magic, les_cs;
+    float les_k;  // 2 sqrt(2) C_S^2 * 9, the Smagorinsky closure's constant
+  } f;
 };
 
 struct Dev {
@@ -82,6 +95,7 @@ struct Dev {
   int* l_new;
   int* l_l2i;
   int* l_recv;
+  int* l_tiles;       // tiles (256 cells along x of one row) holding liquid cells
   Ctrl* ctrl;
   double* trace;      // kTraceCapacity * 3 doubles
   double* red;        // reduction scratch, kReduceBlocks * 2 doubles
@@ -106,9 +120,12 @@ struct Launch {
   // decode plane i of pdf[cur] into dst (device, nx*ny*nz doubles, unpadded)
   cudaError_t (*export_pdf)(const Dev&, const Geom&, const Phys&, int cur, int i, double* dst,
                             cudaStream_t);
-  // the bulk stream-collide kernel alone (timing); leaves ctrl->n_if set
+  // work lists the bulk kernel needs (interface cells, liquid tiles), or null
+  cudaError_t (*pre_bulk)(const Dev&, const Geom&, const Phys&, cudaStream_t);
+  // the bulk stream-collide kernel alone (timing)
   cudaError_t (*stream_collide)(const Dev&, const Geom&, const Phys&, cudaStream_t);
-  int launches_per_step;
+  // kernel launches of one step
+  int (*launches_per_step)(const Geom&);
 };
 
 // Launch tables, one translation unit per (storage, lattice).

@@ -30,6 +30,10 @@
 
 namespace fsl {
 
+// A physical parameter in the arithmetic type R: the FP64 value for the FP64
+// path, the copy rounded once on the host otherwise.
+#define PAR(R, p, name) (sizeof(R) == 8 ? (R)(p).name : (R)(p).f.name)
+
 #define FSL_GRID_LOOP(k, n) \
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < (n); k += gridDim.x * blockDim.x)
 // Warp-synchronous grid loop: all lanes of a warp run the same iterations
@@ -124,7 +128,7 @@ __device__ __forceinline__ R collide(const R* fin, R* fout, const Phys& p, R& rh
   R rho, drho, jx, jy, jz;
   density<Q, SHIFT, R>(fin, rho, drho);
   momentum<Q, R>(fin, jx, jy, jz);
-  const R gx = (R)p.g[0], gy = (R)p.g[1], gz = (R)p.g[2];
+  const R gx = PAR(R, p, g[0]), gy = PAR(R, p, g[1]), gz = PAR(R, p, g[2]);
   // Eq. nm-lbm-velocity with F = rho g: u = j / rho + g / 2
   const R ux = jx / rho + (R)0.5 * gx, uy = jy / rho + (R)0.5 * gy, uz = jz / rho + (R)0.5 * gz;
   const R Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
@@ -132,12 +136,39 @@ __device__ __forceinline__ R collide(const R* fin, R* fout, const Phys& p, R& rh
   R fe[Q], fg[Q];
   feq_all<Q, SHIFT, R>(fe, rho, drho, ux, uy, uz, usq);
   guo_all<Q, R>(fg, ux, uy, uz, Fx, Fy, Fz);
+  R om = PAR(R, p, omega), pre = PAR(R, p, pre_e);
+  R le = PAR(R, p, lam_e), lo = PAR(R, p, lam_o), pe = PAR(R, p, pre_e), po = PAR(R, p, pre_o);
+  if (p.les_cs > 0.0) {
+    // Smagorinsky model (Sec. 2.1): Q_ab = sum_i c_ia c_ib (f_i - f_i^eq),
+    // Qbar = sqrt(2 sum_ab Q_ab^2),
+    // tau = tau0 + (sqrt(tau0^2 + 2 sqrt(2) C_S^2 Qbar / (rho c_s^4)) - tau0) / 2
+    R qq = (R)0;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        R qab = (R)0;
+#pragma unroll
+        for (int i = 1; i < Q; ++i) {
+          const int cc = dir_c(i, a) * dir_c(i, b);
+          if (cc != 0) qab = qab + (R)cc * (fin[i] - fe[i]);
+        }
+        qq = qq + qab * qab;
+      }
+    const R qbar = sqrt((R)2 * qq);
+    const R t0 = PAR(R, p, tau), cs = PAR(R, p, les_cs);
+    const R tau = t0 + (R)0.5 * (sqrt(t0 * t0 + (R)2 * sqrt((R)2) * cs * cs * qbar * (R)9 / rho) - t0);
+    om = (R)1 / tau;
+    pre = (R)1 - (R)0.5 * om;
+    le = om;
+    lo = (R)1 / ((R)0.5 + PAR(R, p, magic) / ((R)1 / le - (R)0.5));
+    pe = (R)1 - (R)0.5 * le;
+    po = (R)1 - (R)0.5 * lo;
+  }
   if (!p.trt) {
-    const R om = (R)p.omega, pre = (R)p.pre_e;
 #pragma unroll
     for (int i = 0; i < Q; ++i) fout[i] = fin[i] - om * (fin[i] - fe[i]) + pre * fg[i];
   } else {
-    const R le = (R)p.lam_e, lo = (R)p.lam_o, pe = (R)p.pre_e, po = (R)p.pre_o;
     fout[0] = fin[0] - le * (fin[0] - fe[0]) + pe * fg[0];
 #pragma unroll
     for (int i = 1; i < Q; i += 2) {
@@ -153,14 +184,27 @@ __device__ __forceinline__ R collide(const R* fin, R* fout, const Phys& p, R& rh
   return usq;
 }
 
+// direction with the components in mask (bit a = axis a) negated
+template <int Q>
+__device__ inline int mirror_dir(int i, int mask) {
+  const int c0 = (mask & 1) ? -rc(i, 0) : rc(i, 0);
+  const int c1 = (mask & 2) ? -rc(i, 1) : rc(i, 1);
+  const int c2 = (mask & 4) ? -rc(i, 2) : rc(i, 2);
+  for (int j = 0; j < Q; ++j)
+    if (rc(j, 0) == c0 && rc(j, 1) == c1 && rc(j, 2) == c2) return j;
+  return i;
+}
+
 // Neighbour coordinates of (x, y, z) along each axis: index 0 -> -1, 1 -> 0,
 // 2 -> +1; -1 beyond a wall.
 struct Nbr {
   int X[3], Y[3], Z[3];
   int sx, ny;
+  int fs;  // free-slip axes
   __device__ __forceinline__ void setup(const Geom& g, int x, int y, int z) {
     sx = g.sx;
     ny = g.ny;
+    fs = g.free_slip;
     X[1] = x; Y[1] = y; Z[1] = z;
     X[0] = x > 0 ? x - 1 : (g.periodic[0] ? g.nx - 1 : -1);
     X[2] = x < g.nx - 1 ? x + 1 : (g.periodic[0] ? 0 : -1);
@@ -177,6 +221,25 @@ struct Nbr {
   // same, for a cell known to have no wall in its stencil
   __device__ __forceinline__ int in(int dx, int dy, int dz) const {
     return X[dx + 1] + sx * (Y[dy + 1] + ny * Z[dz + 1]);
+  }
+  // Where the PDF f_i arriving at the cell comes from: normally the cell
+  // x - c_i, direction i; across free-slip walls (specular reflection) the
+  // cell x - c_i with the crossed components removed, in the mirrored
+  // direction.  -1 for a no-slip wall or an obstacle (halfway bounce-back).
+  template <int Q>
+  __device__ __forceinline__ int source(int i, const uint8_t* flags, int& dir) const {
+    int a = X[1 - dir_c(i, 0)], b = Y[1 - dir_c(i, 1)], c = Z[1 - dir_c(i, 2)];
+    const int crossed = (a < 0 ? 1 : 0) | (b < 0 ? 2 : 0) | (c < 0 ? 4 : 0);
+    dir = i;
+    if (crossed) {
+      if ((crossed & fs) != crossed) return -1;
+      if (a < 0) a = X[1];
+      if (b < 0) b = Y[1];
+      if (c < 0) c = Z[1];
+      dir = mirror_dir<Q>(i, crossed);
+    }
+    const int n = a + sx * (b + ny * c);
+    return (flags[n] & F_TYPE) == T_OBST ? -1 : n;
   }
 };
 
@@ -195,10 +258,10 @@ __device__ __forceinline__ void pull_liquid(const typename ST::T* __restrict__ A
   } else {
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      int n = nb.at(-dir_c(i, 0), -dir_c(i, 1), -dir_c(i, 2));
-      int t = type_at(flags, n);
-      if (t == T_OBST) fin[i] = ST::ldw(A + opp(i) * plane + c); /* halfway bounce-back */
-      else fin[i] = ST::ldw(A + i * plane + n);
+      int di;
+      const int n = nb.source<Q>(i, flags, di);
+      if (n < 0) fin[i] = ST::ldw(A + opp(i) * plane + c); /* halfway bounce-back */
+      else fin[i] = ST::ldw(A + di * plane + n);            /* neighbour or mirror image */
     }
   }
 }
@@ -212,66 +275,185 @@ __device__ __forceinline__ void pull_liquid(const typename ST::T* __restrict__ A
 //   f*_i  = f_i  - [lam_e (f+ - e+) - pe G+] - [lam_o (f- - e-) - po G-]
 //   f*_i' = f_i' - [lam_e (f+ - e+) - pe G+] + [lam_o (f- - e-) - po G-]
 // which is the TRT update with Guo forcing; SRT is lam_o = lam_e = omega.
-template <int Q>
-__device__ __forceinline__ float collide_lp(const float* f, float* o, float lamE, float lamO,
-                                            float pe, float po, float gx, float gy, float gz,
-                                            float S, float& rho_out) {
+// Smagorinsky parameters of the 16/32-bit collision (cs = 0: model off)
+struct LesLp {
+  float cs, tau0, magic, k;  // k = 2 sqrt(2) C_S^2 * 9 (c_s^-4 of the closure)
+  int trt;
+  __host__ __device__ static LesLp of(const Phys& p) {
+    return LesLp{p.f.les_cs, p.f.tau, p.f.magic, p.f.les_k, p.trt};
+  }
+};
+
+// Arithmetic of the 16/32-bit collision on V = float (one cell) or float2 (two
+// cells, the packed FP32 instructions of sm_100+).  Every operation is an
+// explicitly rounded add, multiply or fused multiply-add, so the compiler
+// contracts nothing and the one-cell and two-cell kernels produce identical
+// bits.
+__device__ __forceinline__ float vsplat(float s, float) { return s; }
+__device__ __forceinline__ float2 vsplat(float s, float2) { return make_float2(s, s); }
+__device__ __forceinline__ float vadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float vsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float vmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float vfma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as fma(b, -1, a): one rounding of the exact difference
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) {
+  return __ffma2_rn(b, make_float2(-1.f, -1.f), a);
+}
+__device__ __forceinline__ float2 vmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 vfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+template <class V> struct Lanes;
+template <> struct Lanes<float> {
+  static constexpr int n = 1;
+  static __device__ __forceinline__ float& at(float& v, int) { return v; }
+};
+template <> struct Lanes<float2> {
+  static constexpr int n = 2;
+  static __device__ __forceinline__ float& at(float2& v, int k) { return k ? v.y : v.x; }
+};
+// sum_k c_k v_k for constant c in {-1, 0, 1}, starting from the first
+// nonzero term (at least one is nonzero for every moving direction)
+template <class V>
+__device__ __forceinline__ V vdot(int a, int b, int c, V x, V y, V z) {
+  V acc = vsplat(0.f, x);
+  bool has = false;
+  if (a == 1) { acc = x; has = true; }
+  if (a == -1) { acc = vsub(vsplat(0.f, x), x); has = true; }
+  if (b != 0) acc = has ? (b == 1 ? vadd(acc, y) : vsub(acc, y)) : (b == 1 ? y : vsub(vsplat(0.f, x), y));
+  has = has || b != 0;
+  if (c != 0) acc = has ? (c == 1 ? vadd(acc, z) : vsub(acc, z)) : (c == 1 ? z : vsub(vsplat(0.f, x), z));
+  return acc;
+}
+
+template <int Q, class V>
+__device__ __forceinline__ V collide_v(const V* f, V* o, float lamE_, float lamO_, float pe_,
+                                       float po_, float gx, float gy, float gz, float S,
+                                       const LesLp& les) {
   constexpr int NP = (Q - 1) / 2;
-  float sp[NP], dp[NP];
+  const V z0 = vsplat(0.f, f[0]);
+  V sp[NP], dp[NP];
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
-    sp[k] = f[2 * k + 1] + f[2 * k + 2];
-    dp[k] = f[2 * k + 1] - f[2 * k + 2];
+    sp[k] = vadd(f[2 * k + 1], f[2 * k + 2]);
+    dp[k] = vsub(f[2 * k + 1], f[2 * k + 2]);
   }
-  float acc = f[0];
+  V acc = f[0];
 #pragma unroll
-  for (int k = 0; k < NP; ++k) acc = acc + sp[k];
-  const float drho = __fmul_rn(acc, 1.0f / S);
-  const float rho = 1.0f + drho;
-  float jx = 0.f, jy = 0.f, jz = 0.f;
+  for (int k = 0; k < NP; ++k) acc = vadd(acc, sp[k]);
+  const V drho = vmul(acc, vsplat(1.0f / S, z0));
+  const V rho = vadd(vsplat(1.0f, z0), drho);
+  // momentum: first contribution assigned, the rest added in direction order
+  V jx = z0, jy = z0, jz = z0;
+  bool hx = false, hy = false, hz = false;
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int i = 2 * k + 1;
-    if (dir_c(i, 0) == 1) jx += dp[k]; else if (dir_c(i, 0) == -1) jx -= dp[k];
-    if (dir_c(i, 1) == 1) jy += dp[k]; else if (dir_c(i, 1) == -1) jy -= dp[k];
-    if (dir_c(i, 2) == 1) jz += dp[k]; else if (dir_c(i, 2) == -1) jz -= dp[k];
+    const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
+    if (c0 != 0) { jx = hx ? (c0 == 1 ? vadd(jx, dp[k]) : vsub(jx, dp[k])) : (c0 == 1 ? dp[k] : vsub(z0, dp[k])); hx = true; }
+    if (c1 != 0) { jy = hy ? (c1 == 1 ? vadd(jy, dp[k]) : vsub(jy, dp[k])) : (c1 == 1 ? dp[k] : vsub(z0, dp[k])); hy = true; }
+    if (c2 != 0) { jz = hz ? (c2 == 1 ? vadd(jz, dp[k]) : vsub(jz, dp[k])) : (c2 == 1 ? dp[k] : vsub(z0, dp[k])); hz = true; }
   }
-  const float kk = (1.0f / S) / rho;
-  const float ux = fmaf(jx, kk, 0.5f * gx), uy = fmaf(jy, kk, 0.5f * gy), uz = fmaf(jz, kk, 0.5f * gz);
-  const float Fx = rho * gx, Fy = rho * gy, Fz = rho * gz;
-  const float usq = ux * ux + uy * uy + uz * uz;
-  const float uF = ux * Fx + uy * Fy + uz * Fz;
-  const float cst = drho - 1.5f * rho * usq;
+  // 1/(S rho) from the hardware reciprocal (relative error below 2^-22,
+  // the same instruction in every variant); S is a power of two
+  V kk = rho;
+#pragma unroll
+  for (int l = 0; l < Lanes<V>::n; ++l) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(Lanes<V>::at(kk, l)));
+    Lanes<V>::at(kk, l) = __fmul_rn(r, 1.0f / S);
+  }
+  const V ux = vfma(jx, kk, vsplat(0.5f * gx, z0));
+  const V uy = vfma(jy, kk, vsplat(0.5f * gy, z0));
+  const V uz = vfma(jz, kk, vsplat(0.5f * gz, z0));
+  const V Fx = vmul(rho, vsplat(gx, z0)), Fy = vmul(rho, vsplat(gy, z0)), Fz = vmul(rho, vsplat(gz, z0));
+  const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
+  const V uF = vfma(uz, Fz, vfma(uy, Fy, vmul(ux, Fx)));
+  const V cst = vfma(vmul(rho, vsplat(-1.5f, z0)), usq, drho);
   // per weight class (index = |c|^2): constants in storage units
-  float A[4], Bc[4], O[4], GU[4], G9[4], G3[4];
+  V A[4], Bc[4], O[4], GU[4], G9[4], G3[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
     const float w = (float)wgt<Q>(c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 7 : (Q == 27 ? 19 : 7));
-    A[c] = (4.5f * w * S) * rho;
-    Bc[c] = (w * S) * cst;
-    O[c] = (3.0f * w * S) * rho;
-    GU[c] = (-3.0f * w * S * pe) * uF;
-    G9[c] = 9.0f * w * S * pe;
-    G3[c] = 3.0f * w * S * po;
+    A[c] = vmul(vsplat(4.5f * w * S, z0), rho);
+    Bc[c] = vmul(vsplat(w * S, z0), cst);
+    O[c] = vmul(vsplat(3.0f * w * S, z0), rho);
   }
-  o[0] = f[0] - fmaf(lamE, f[0] - Bc[0], -GU[0]);
+  V lamE = vsplat(lamE_, z0), lamO = vsplat(lamO_, z0), pe = vsplat(pe_, z0), po = vsplat(po_, z0);
+  if (les.cs > 0.f) {
+    // Smagorinsky model (Sec. 2.1) in the pair form: Q_ab = sum_i c_ia c_ib
+    // (f_i - f_i^eq) = sum_pairs c_a c_b (f_i + f_i' - 2 e+)
+    V qxx = z0, qyy = z0, qzz = z0, qxy = z0, qxz = z0, qyz = z0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int i = 2 * k + 1;
+      const int c = len2(i);
+      const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
+      const V cu = vdot(c0, c1, c2, ux, uy, uz);
+      const V dn = vsub(sp[k], vmul(vsplat(2.f, z0), vfma(vmul(A[c], cu), cu, Bc[c])));
+      if (c0 != 0) qxx = vadd(qxx, dn);
+      if (c1 != 0) qyy = vadd(qyy, dn);
+      if (c2 != 0) qzz = vadd(qzz, dn);
+      if (c0 * c1 == 1) qxy = vadd(qxy, dn); else if (c0 * c1 == -1) qxy = vsub(qxy, dn);
+      if (c0 * c2 == 1) qxz = vadd(qxz, dn); else if (c0 * c2 == -1) qxz = vsub(qxz, dn);
+      if (c1 * c2 == 1) qyz = vadd(qyz, dn); else if (c1 * c2 == -1) qyz = vsub(qyz, dn);
+    }
+    const V dg = vfma(qzz, qzz, vfma(qyy, qyy, vmul(qxx, qxx)));
+    const V of = vfma(qyz, qyz, vfma(qxz, qxz, vmul(qxy, qxy)));
+    const V qq = vfma(vsplat(2.f, z0), of, dg);
+    V rq = qq, rr = rho;
+#pragma unroll
+    for (int l = 0; l < Lanes<V>::n; ++l) {
+      // Q̄ = sqrt(2 Q_ab Q_ab) in lattice units; tau from the quadratic of
+      // the Smagorinsky closure
+      const float qbar = __fmul_rn(__fsqrt_rn(__fmul_rn(2.f, Lanes<V>::at(rq, l))), 1.0f / S);
+      const float t0 = les.tau0;
+      const float arg = __fmaf_rn(t0, t0, __fdiv_rn(__fmul_rn(les.k, qbar), Lanes<V>::at(rr, l)));
+      const float tau = __fmaf_rn(0.5f, __fsub_rn(__fsqrt_rn(arg), t0), t0);
+      const float le = __frcp_rn(tau);
+      const float lo = les.trt ? __frcp_rn(__fadd_rn(0.5f, __fdiv_rn(les.magic, __fsub_rn(tau, 0.5f)))) : le;
+      Lanes<V>::at(lamE, l) = le;
+      Lanes<V>::at(lamO, l) = lo;
+      Lanes<V>::at(pe, l) = __fmaf_rn(-0.5f, le, 1.f);
+      Lanes<V>::at(po, l) = __fmaf_rn(-0.5f, lo, 1.f);
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float w = (float)wgt<Q>(c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 7 : (Q == 27 ? 19 : 7));
+    GU[c] = vmul(vmul(vsplat(-3.0f * w * S, z0), pe), uF);
+    G9[c] = vmul(vsplat(9.0f * w * S, z0), pe);
+    G3[c] = vmul(vsplat(3.0f * w * S, z0), po);
+  }
+  // rest population: f0 - [lam_e (f0 - e0) - pe G0]
+  o[0] = vadd(f[0], vfma(lamE, vsub(Bc[0], f[0]), GU[0]));
+  const V m05 = vsplat(-0.5f, z0);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int i = 2 * k + 1;
     const int c = len2(i);
-    const float cu = dot3r(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2), ux, uy, uz);
-    const float cF = dot3r(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2), Fx, Fy, Fz);
-    const float e = fmaf(A[c] * cu, cu, Bc[c]);
-    const float od = O[c] * cu;
-    const float Gp = fmaf(G9[c] * cu, cF, GU[c]);
-    const float Gm = G3[c] * cF;
-    const float Dp = fmaf(lamE, fmaf(0.5f, sp[k], -e), -Gp);
-    const float Dm = fmaf(lamO, fmaf(0.5f, dp[k], -od), -Gm);
-    o[i] = f[i] - Dp - Dm;
-    o[i + 1] = f[i + 1] - Dp + Dm;
+    const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
+    const V cu = vdot(c0, c1, c2, ux, uy, uz);
+    const V cF = vdot(c0, c1, c2, Fx, Fy, Fz);
+    const V e = vfma(vmul(A[c], cu), cu, Bc[c]);
+    const V od = vmul(O[c], cu);
+    const V Gp = vfma(vmul(G9[c], cu), cF, GU[c]);
+    const V Gm = vmul(G3[c], cF);
+    // minus the even and odd corrections: lam (e - f+/2... ) + G, each the
+    // exact negation of lam (f+/2 - e) - G
+    const V nDp = vfma(lamE, vfma(m05, sp[k], e), Gp);
+    const V nDm = vfma(lamO, vfma(m05, dp[k], od), Gm);
+    o[i] = vadd(vadd(f[i], nDp), nDm);
+    o[i + 1] = vsub(vadd(f[i + 1], nDp), nDm);
   }
-  rho_out = rho;
   return usq;
+}
+
+template <int Q>
+__device__ __forceinline__ float collide_lp(const float* f, float* o, float lamE, float lamO,
+                                            float pe, float po, float gx, float gy, float gz,
+                                            float S, const LesLp& les, float& rho_out) {
+  rho_out = 0.f;
+  return collide_v<Q, float>(f, o, lamE, lamO, pe, po, gx, gy, gz, S, les);
 }
 
 // Bulk pass of the 16/32-bit path: two cells (x0, x0+1) per thread, pairs of
@@ -279,8 +461,8 @@ __device__ __forceinline__ float collide_lp(const float* f, float* o, float lamE
 // x -/+ 1 come from the neighbouring lane by a warp shuffle (one extra
 // scalar load at the warp's edge or at a periodic wrap).  Liquid cells next
 // to a wall or obstacle take the per-direction bounce-back path.
-template <int Q, class ST>
-__global__ void __launch_bounds__(128) k_stream_collide_lp(Dev d, Geom g, Phys p) {
+template <int Q, class ST, int BT, int MINB, bool PACKED>
+__global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, Phys p) {
   using T = typename ST::T;
   constexpr float S = ST::kScaleF;
   Ctrl* ctrl = d.ctrl;
@@ -318,69 +500,376 @@ __global__ void __launch_bounds__(128) k_stream_collide_lp(Dev d, Geom g, Phys p
   const int xm = x0 > 0 ? xc - 1 : (g.periodic[0] ? g.nx - 1 : 0);
   const bool edge_hi = (lane == 31) || (x0 + 2 >= g.nx);
   const int xp = (x0 + 2 < g.nx) ? x0 + 2 : ((g.periodic[0] && x0 + 2 == g.nx) ? 0 : xc);
-  float fa[Q], fb[Q];
+  const bool wrap0 = g.periodic[0] && x0 + 1 == g.nx;
+  // f[i] = (value pulled by cell x0, value pulled by cell x0 + 1)
+  float2 f[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
     const T* base = A + i * P + (long long)g.sx * (Yr[1 - cy] + g.ny * Zr[1 - cz]);
     const float2 v = ST::ld2(base + xc);
     if (cx == 0) {
-      fa[i] = v.x;
-      fb[i] = v.y;
+      f[i] = v;
     } else if (cx == 1) {  // pulled from x - 1
       const float up = __shfl_up_sync(FULL, v.y, 1);
-      fa[i] = (lane == 0) ? ST::ld1(base + xm) : up;
-      fb[i] = v.x;
+      f[i] = make_float2((lane == 0) ? ST::ld1(base + xm) : up, v.x);
     } else {  // pulled from x + 1
       const float dn = __shfl_down_sync(FULL, v.x, 1);
-      fa[i] = v.y;
-      fb[i] = edge_hi ? ST::ld1(base + xp) : dn;
+      f[i] = make_float2(v.y, edge_hi ? ST::ld1(base + xp) : dn);
+      // odd periodic width: the pair's first cell ends the row and wraps
+      if (wrap0) f[i].x = ST::ld1(base);
+    }
+  }
+  if ((liq0 && (fl0 & F_NEAR_OBST)) || (liq1 && (fl1 & F_NEAR_OBST))) {
+    float t[Q];
+    if (liq0 && (fl0 & F_NEAR_OBST)) {
+      Nbr nb;
+      nb.setup(g, x0, y, z);
+      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0, true, t);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i].x = t[i] * S;
+    }
+    if (liq1 && (fl1 & F_NEAR_OBST)) {
+      Nbr nb;
+      nb.setup(g, x0 + 1, y, z);
+      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0 + 1, true, t);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i].y = t[i] * S;
     }
   }
   const bool tr = p.trt != 0;
-  const float lamE = (float)p.lam_e, lamO = tr ? (float)p.lam_o : (float)p.omega;
-  const float pe = (float)p.pre_e, po = tr ? (float)p.pre_o : (float)p.pre_e;
-  const float gx = (float)p.g[0], gy = (float)p.g[1], gz = (float)p.g[2];
-  bool bad = false;
-  float o0[Q], o1[Q];
-  if (liq0) {
-    if (fl0 & F_NEAR_OBST) {
-      Nbr nb;
-      nb.setup(g, x0, y, z);
-      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0, true, fa);
+  const float lamE = p.f.lam_e, lamO = tr ? p.f.lam_o : p.f.omega;
+  const float pe = p.f.pre_e, po = tr ? p.f.pre_o : p.f.pre_e;
+  float2 usq;
+  if constexpr (PACKED) {
+    // both cells collide together in packed FP32 (a non-liquid partner's
+    // result is discarded)
+    usq = collide_v<Q, float2>(f, f, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2], S,
+                               LesLp::of(p));
+  } else {
+    // one cell after the other: fewer values live at once
+    usq = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fa[i] *= S;
-    }
-    float rho;
-    const float usq = collide_lp<Q>(fa, o0, lamE, lamO, pe, po, gx, gy, gz, S, rho);
-    bad |= !(usq < (float)(1.0 / 3.0));
-  }
-  if (liq1) {
-    if (fl1 & F_NEAR_OBST) {
-      Nbr nb;
-      nb.setup(g, x0 + 1, y, z);
-      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0 + 1, true, fb);
+    for (int h = 0; h < 2; ++h) {
+      if (!(h ? liq1 : liq0)) continue;
+      float c[Q];
 #pragma unroll
-      for (int i = 0; i < Q; ++i) fb[i] *= S;
+      for (int i = 0; i < Q; ++i) c[i] = Lanes<float2>::at(f[i], h);
+      Lanes<float2>::at(usq, h) =
+          collide_v<Q, float>(c, c, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2], S, LesLp::of(p));
+#pragma unroll
+      for (int i = 0; i < Q; ++i) Lanes<float2>::at(f[i], h) = c[i];
     }
-    float rho;
-    const float usq = collide_lp<Q>(fb, o1, lamE, lamO, pe, po, gx, gy, gz, S, rho);
-    bad |= !(usq < (float)(1.0 / 3.0));
   }
+  const bool bad = (liq0 && !(usq.x < (float)(1.0 / 3.0))) || (liq1 && !(usq.y < (float)(1.0 / 3.0)));
   T* out = B + row + x0;
   if (liq0 && liq1) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) ST::st2(out + i * P, o0[i], o1[i]);
+    for (int i = 0; i < Q; ++i) ST::st2(out + i * P, f[i].x, f[i].y);
   } else if (liq0) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) ST::st1(out + i * P, o0[i]);
+    for (int i = 0; i < Q; ++i) ST::st1(out + i * P, f[i].x);
   } else if (liq1) {
 #pragma unroll
-    for (int i = 0; i < Q; ++i) ST::st1(out + i * P + 1, o1[i]);
+    for (int i = 0; i < Q; ++i) ST::st1(out + i * P + 1, f[i].y);
   }
   if (__any_sync(FULL, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
 }
 
+
+// Bulk pass of the 16-bit storages with four cells per thread: the four
+// stored values of each direction arrive as one aligned 8-byte load and stay
+// packed (two 32-bit words) until the collision unpacks them; the values
+// pulled from x -/+ 1 are assembled with byte permutes from the neighbouring
+// lane's words (warp shuffles), one scalar load at the warp's edges or at a
+// periodic wrap.  Same arithmetic as k_stream_collide_lp, twice the bytes in
+// flight per thread.
+template <int Q, class ST>
+__global__ void __launch_bounds__(64) k_stream_collide_lp4(Dev d, Geom g, Phys p) {
+  using T = typename ST::T;
+  static_assert(sizeof(T) == 2, "16-bit storage only");
+  constexpr float S = ST::kScaleF;
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int cur = ctrl->step & 1;
+  const T* __restrict__ A = (const T*)d.pdf[cur];
+  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
+  const long long P = g.plane;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int x0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y, z = blockIdx.z;
+  const int row = g.sx * (y + g.ny * z);
+  const bool in_row = x0 < g.sx;
+  const int xc = in_row ? x0 : g.sx - 4;  // clamped group start for addressing
+  uint8_t fl[4] = {0, 0, 0, 0};
+  if (in_row) {
+    const uchar4 f4 = *reinterpret_cast<const uchar4*>(d.flags + row + x0);
+    fl[0] = x0 < g.nx ? f4.x : (uint8_t)T_GAS;
+    fl[1] = x0 + 1 < g.nx ? f4.y : (uint8_t)T_GAS;
+    fl[2] = x0 + 2 < g.nx ? f4.z : (uint8_t)T_GAS;
+    fl[3] = x0 + 3 < g.nx ? f4.w : (uint8_t)T_GAS;
+  }
+  bool anyl = false;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    warp_append((fl[k] & F_TYPE) == T_IF, row + x0 + k, &ctrl->n_if, d.l_if);
+    anyl |= (fl[k] & F_TYPE) == T_LIQ;
+  }
+  if (!__any_sync(FULL, anyl)) return;
+  int Yr[3], Zr[3];
+  Yr[1] = y; Zr[1] = z;
+  Yr[0] = y > 0 ? y - 1 : (g.periodic[1] ? g.ny - 1 : y);
+  Yr[2] = y < g.ny - 1 ? y + 1 : (g.periodic[1] ? 0 : y);
+  Zr[0] = z > 0 ? z - 1 : (g.periodic[2] ? g.nz - 1 : z);
+  Zr[2] = z < g.nz - 1 ? z + 1 : (g.periodic[2] ? 0 : z);
+  const int xm = x0 > 0 ? xc - 1 : (g.periodic[0] ? g.nx - 1 : 0);
+  const bool edge_hi = (lane == 31) || (x0 + 4 >= g.nx);
+  const int xp = (x0 + 4 < g.nx) ? x0 + 4 : ((g.periodic[0] && x0 + 4 == g.nx) ? 0 : xc);
+  const int kwrap = (g.periodic[0] && x0 < g.nx && x0 + 3 >= g.nx) ? g.nx - 1 - x0 : -1;
+  // w[i][0] = (e0, e1), w[i][1] = (e2, e3): the four values pulled by the
+  // thread's cells in direction i, low half first
+  unsigned w[Q][2];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
+    const T* base = A + i * P + (long long)g.sx * (Yr[1 - cy] + g.ny * Zr[1 - cz]);
+    const uint2 v = __ldg(reinterpret_cast<const uint2*>(base + xc));
+    if (cx == 0) {
+      w[i][0] = v.x;
+      w[i][1] = v.y;
+    } else if (cx == 1) {  // pulled from x - 1: (left, e0), (e1, e2)
+      unsigned left = __shfl_up_sync(FULL, v.y, 1);
+      if (lane == 0) left = (unsigned)__ldg(reinterpret_cast<const unsigned short*>(base + xm)) << 16;
+      w[i][0] = __byte_perm(left, v.x, 0x5432);
+      w[i][1] = __byte_perm(v.x, v.y, 0x5432);
+    } else {  // pulled from x + 1: (e1, e2), (e3, right)
+      unsigned right = __shfl_down_sync(FULL, v.x, 1);
+      if (edge_hi) right = (unsigned)__ldg(reinterpret_cast<const unsigned short*>(base + xp));
+      w[i][0] = __byte_perm(v.x, v.y, 0x5432);
+      w[i][1] = __byte_perm(v.y, right, 0x5432);
+      // periodic row end inside the group (cells 0..2): wraps to x = 0
+      if (kwrap >= 0) {
+        const unsigned e = (unsigned)__ldg(reinterpret_cast<const unsigned short*>(base));
+        if (kwrap == 0) w[i][0] = (w[i][0] & 0xffff0000u) | e;
+        else if (kwrap == 1) w[i][0] = (w[i][0] & 0xffffu) | (e << 16);
+        else w[i][1] = (w[i][1] & 0xffff0000u) | e;
+      }
+    }
+  }
+  const bool tr = p.trt != 0;
+  const float lamE = p.f.lam_e, lamO = tr ? p.f.lam_o : p.f.omega;
+  const float pe = p.f.pre_e, po = tr ? p.f.pre_o : p.f.pre_e;
+  const float gx = p.f.g[0], gy = p.f.g[1], gz = p.f.g[2];
+  const LesLp les = LesLp::of(p);
+  bool bad = false;
+#pragma unroll
+  for (int pr = 0; pr < 2; ++pr) {  // cell pairs (0, 1) and (2, 3)
+    bool liq[2];
+    liq[0] = (fl[2 * pr] & F_TYPE) == T_LIQ;
+    liq[1] = (fl[2 * pr + 1] & F_TYPE) == T_LIQ;
+    if (!liq[0] && !liq[1]) continue;
+    float2 f[Q];
+#pragma unroll
+    for (int i = 0; i < Q; ++i) f[i] = ST::unpack2(w[i][pr]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * pr + h;
+      if (liq[h] && (fl[k] & F_NEAR_OBST)) {
+        float t[Q];
+        Nbr nb;
+        nb.setup(g, x0 + k, y, z);
+        pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0 + k, true, t);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Lanes<float2>::at(f[i], h) = t[i] * S;
+      }
+    }
+    // both cells of the pair collide together in packed FP32
+    const float2 usq = collide_v<Q, float2>(f, f, lamE, lamO, pe, po, gx, gy, gz, S, les);
+    bad |= (liq[0] && !(usq.x < (float)(1.0 / 3.0))) || (liq[1] && !(usq.y < (float)(1.0 / 3.0)));
+#pragma unroll
+    for (int i = 0; i < Q; ++i) w[i][pr] = ST::pack2(f[i].x, f[i].y);
+    T* out = B + row + x0 + 2 * pr;
+    if (liq[0] && liq[1]) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(out + i * P) = w[i][pr];
+    } else if (liq[0]) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        *reinterpret_cast<unsigned short*>(out + i * P) = (unsigned short)(w[i][pr] & 0xffffu);
+    } else if (liq[1]) {
+#pragma unroll
+      for (int i = 0; i < Q; ++i)
+        *reinterpret_cast<unsigned short*>(out + i * P + 1) = (unsigned short)(w[i][pr] >> 16);
+    }
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
+// Bulk pass of the 16-bit storages, software-pipelined over rows: each block
+// covers 256 cells of a row (two per thread) and walks rows r, r + G, r + 2G,
+// ... of the domain; while it collides row r, the loads of its next row are
+// already in flight (one aligned 4-byte word per direction and thread, plus
+// the scalar values the warp's edge lanes need), and the flags are read two
+// rows ahead so that the decision to load a row (any liquid cell in the warp)
+// never waits.  The loads in flight therefore cover the whole collision
+// instead of only the start of a thread's life.
+template <int Q, class ST>
+__device__ __forceinline__ void pp_fetch(const typename ST::T* __restrict__ A, const Geom& g,
+                                         int rr, int xc, int xm, int xp, bool edge_hi, bool wrap0,
+                                         int lane, unsigned* w, unsigned* e) {
+  const long long P = g.plane;
+  const int y = rr % g.ny, z = rr / g.ny;
+  int Yr[3], Zr[3];
+  Yr[1] = y; Zr[1] = z;
+  Yr[0] = y > 0 ? y - 1 : (g.periodic[1] ? g.ny - 1 : y);
+  Yr[2] = y < g.ny - 1 ? y + 1 : (g.periodic[1] ? 0 : y);
+  Zr[0] = z > 0 ? z - 1 : (g.periodic[2] ? g.nz - 1 : z);
+  Zr[2] = z < g.nz - 1 ? z + 1 : (g.periodic[2] ? 0 : z);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
+    const unsigned short* base = reinterpret_cast<const unsigned short*>(A) + i * P +
+                                 (long long)g.sx * (Yr[1 - cy] + g.ny * Zr[1 - cz]);
+    w[i] = __ldg(reinterpret_cast<const unsigned*>(base + xc));
+    e[i] = 0u;
+    if (cx == 1 && lane == 0) e[i] = (unsigned)__ldg(base + xm) << 16;
+    if (cx == -1 && (wrap0 || edge_hi)) e[i] = (unsigned)__ldg(base + (wrap0 ? 0 : xp));
+  }
+}
+
+template <int Q, class ST>
+__global__ void __launch_bounds__(128, 3) k_stream_collide_pp(Dev d, Geom g, Phys p) {
+  using T = typename ST::T;
+  static_assert(sizeof(T) == 2, "16-bit storage only");
+  constexpr float S = ST::kScaleF;
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int cur = ctrl->step & 1;
+  const T* __restrict__ A = (const T*)d.pdf[cur];
+  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
+  const long long P = g.plane;
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int nrows = g.ny * g.nz;
+  const int G = gridDim.y;
+  int r = blockIdx.y;
+  if (r >= nrows) return;
+  const bool in_row = x0 < g.sx;
+  const int xc = in_row ? x0 : g.sx - 2;
+  const int xm = x0 > 0 ? xc - 1 : (g.periodic[0] ? g.nx - 1 : 0);
+  const bool edge_hi = (lane == 31) || (x0 + 2 >= g.nx);
+  const int xp = (x0 + 2 < g.nx) ? x0 + 2 : ((g.periodic[0] && x0 + 2 == g.nx) ? 0 : xc);
+  const bool wrap0 = g.periodic[0] && x0 + 1 == g.nx;
+  // the two type bytes of the thread's cells in row rr (gas outside)
+  auto flags_of = [&](int rr) -> unsigned {
+    if (rr >= nrows || !in_row) return 0u;
+    const uchar2 f = *reinterpret_cast<const uchar2*>(d.flags + (long long)rr * g.sx + x0);
+    const unsigned a = x0 < g.nx ? f.x : (unsigned)T_GAS;
+    const unsigned b = x0 + 1 < g.nx ? f.y : (unsigned)T_GAS;
+    return a | (b << 8);
+  };
+  auto has_liquid = [](unsigned f) {
+    return (f & F_TYPE) == T_LIQ || ((f >> 8) & F_TYPE) == T_LIQ;
+  };
+  const bool tr = p.trt != 0;
+  const float lamE = p.f.lam_e, lamO = tr ? p.f.lam_o : p.f.omega;
+  const float pe = p.f.pre_e, po = tr ? p.f.pre_o : p.f.pre_e;
+  const LesLp les = LesLp::of(p);
+  unsigned fc = flags_of(r), fn = flags_of(r + G);
+  bool anyc = __any_sync(FULL, has_liquid(fc));
+  unsigned w[Q], e[Q];
+  if (anyc) pp_fetch<Q, ST>(A, g, r, xc, xm, xp, edge_hi, wrap0, lane, w, e);
+  bool bad = false;
+  for (;;) {
+    const int rn = r + G;
+    const unsigned fnn = flags_of(rn + G);
+    const bool anyn = __any_sync(FULL, has_liquid(fn));
+    unsigned wn[Q], en[Q];
+    if (anyn) pp_fetch<Q, ST>(A, g, rn, xc, xm, xp, edge_hi, wrap0, lane, wn, en);
+    // row r: interface cells to the list, liquid cells stream and collide
+    const long long row = (long long)r * g.sx;
+    const uint8_t fl0 = (uint8_t)(fc & 0xffu), fl1 = (uint8_t)(fc >> 8);
+    warp_append((fl0 & F_TYPE) == T_IF, (int)(row + x0), &ctrl->n_if, d.l_if);
+    warp_append((fl1 & F_TYPE) == T_IF, (int)(row + x0 + 1), &ctrl->n_if, d.l_if);
+    if (anyc) {
+      const bool liq0 = (fl0 & F_TYPE) == T_LIQ, liq1 = (fl1 & F_TYPE) == T_LIQ;
+      float2 f[Q];
+#pragma unroll
+      for (int i = 0; i < Q; ++i) {
+        const int cx = dir_c(i, 0);
+        unsigned word;
+        if (cx == 0) {
+          word = w[i];
+        } else if (cx == 1) {  // (x - 1, x): the left lane's high half, then ours
+          unsigned left = __shfl_up_sync(FULL, w[i], 1);
+          if (lane == 0) left = e[i];
+          word = __byte_perm(left, w[i], 0x5432);
+        } else {  // (x + 1, x + 2): our high half, then the right lane's low half
+          unsigned right = __shfl_down_sync(FULL, w[i], 1);
+          if (edge_hi) right = e[i];
+          word = wrap0 ? e[i] : __byte_perm(w[i], right, 0x5432);
+        }
+        f[i] = ST::unpack2(word);
+      }
+      const int y = r % g.ny, z = r / g.ny;
+      if ((liq0 && (fl0 & F_NEAR_OBST)) || (liq1 && (fl1 & F_NEAR_OBST))) {
+        float t[Q];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const uint8_t fh = h ? fl1 : fl0;
+          if ((fh & F_TYPE) == T_LIQ && (fh & F_NEAR_OBST)) {
+            Nbr nb;
+            nb.setup(g, x0 + h, y, z);
+            pull_liquid<Q, ST>(A, P, d.flags, nb, (int)(row + x0 + h), true, t);
+#pragma unroll
+            for (int i = 0; i < Q; ++i) Lanes<float2>::at(f[i], h) = t[i] * S;
+          }
+        }
+      }
+      float2 usq = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!(h ? liq1 : liq0)) continue;
+        float c[Q];
+#pragma unroll
+        for (int i = 0; i < Q; ++i) c[i] = Lanes<float2>::at(f[i], h);
+        Lanes<float2>::at(usq, h) =
+            collide_v<Q, float>(c, c, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2], S, les);
+#pragma unroll
+        for (int i = 0; i < Q; ++i) Lanes<float2>::at(f[i], h) = c[i];
+      }
+      bad |= (liq0 && !(usq.x < (float)(1.0 / 3.0))) || (liq1 && !(usq.y < (float)(1.0 / 3.0)));
+      T* out = B + row + x0;
+      if (liq0 && liq1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) *reinterpret_cast<unsigned*>(out + i * P) = ST::pack2(f[i].x, f[i].y);
+      } else if (liq0) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ST::st1(out + i * P, f[i].x);
+      } else if (liq1) {
+#pragma unroll
+        for (int i = 0; i < Q; ++i) ST::st1(out + i * P + 1, f[i].y);
+      }
+    }
+    if (rn >= nrows) break;
+    r = rn;
+    fc = fn;
+    fn = fnn;
+    anyc = anyn;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      w[i] = wn[i];
+      e[i] = en[i];
+    }
+  }
+  if (__any_sync(FULL, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
+}  // namespace fsl
+#include "fsl_bulk.cuh"
+namespace fsl {
 
 // ------------------------------------------------------------ stream-collide
 // Pass over all cells: liquid cells stream and collide here; interface cells
@@ -447,9 +936,9 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
     R rt, drt, jx, jy, jz;
     density<Q, SH, R>(own, rt, drt);
     momentum<Q, R>(own, jx, jy, jz);
-    const R utx = jx / rt - (R)0.5 * (R)p.g[0];
-    const R uty = jy / rt - (R)0.5 * (R)p.g[1];
-    const R utz = jz / rt - (R)0.5 * (R)p.g[2];
+    const R utx = jx / rt - (R)0.5 * PAR(R, p, g[0]);
+    const R uty = jy / rt - (R)0.5 * PAR(R, p, g[1]);
+    const R utz = jz / rt - (R)0.5 * PAR(R, p, g[2]);
     const R utsq = utx * utx + uty * uty + utz * utz;
     const double pg = (p.options & 8u) ? p.p_v - 2.0 * p.sigma * d.kappa[c]
                                        : p.p_v + p.sigma * d.kappa[c];
@@ -457,13 +946,15 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
     const R drg = (R)(3.0 * pg - 1.0);
     R feg[Q];
     feq_all<Q, SH, R>(feg, rg, drg, utx, uty, utz, utsq);
-    int tn[Q];
+    int tn[Q], sn[Q];  // type and cell of each incoming PDF's source
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
-      const int n = nb.at(-dir_c(i, 0), -dir_c(i, 1), -dir_c(i, 2));
+      int di;
+      const int n = nb.source<Q>(i, d.flags, di);
       const int t = type_at(d.flags, n);
       tn[i] = t;
-      if (is_fluid(t)) fin[i] = ST::ldw(A + i * P + n);
+      sn[i] = n;
+      if (is_fluid(t)) fin[i] = ST::ldw(A + di * P + n);      /* neighbour or mirror image */
       else if (t == T_OBST) fin[i] = own[opp(i)];             /* halfway bounce-back */
       else fin[i] = feg[i] + feg[opp(i)] - own[opp(i)];       /* anti-bounce-back from gas */
     }
@@ -477,15 +968,17 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const int io = opp(i);
-      const int t = tn[io];  // the neighbour x + c_i sent f_io
+      // the cell exchanging PDFs with x along c_i (x + c_i, or its mirror
+      // image across a free-slip wall) is the source of the incoming f_io
+      const int t = tn[io];
       if (t != T_LIQ && t != T_IF) continue;
-      // f_in = f*_io(x + c_i) = fin[io], f_out = f*_i(x) = own[i]
+      // f_in = fin[io] (what arrives from it), f_out = f*_i(x) = own[i]
       R dd;
       const R both = fin[io] - own[i];
       if (t == T_LIQ) {
         dd = both;
       } else {
-        const int n = nb.at(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2));
+        const int n = sn[io];
         const int clsn = d.flags[n] & (F_NF | F_NE);
         const R f_in = SH ? fin[io] + (R)wgt<Q>(io) : fin[io];
         const R f_out = SH ? own[i] + (R)wgt<Q>(i) : own[i];
@@ -627,7 +1120,7 @@ static __global__ void __launch_bounds__(256) k_finalise(Dev d) {
       d.flags[c] = (uint8_t)((fl & ~F_TYPE) | T_GAS);
       d.phi[c] = 0.0;
       d.mass[c] = 0.0;
-      atomicAdd(&ctrl->pad[0], 1u);
+      atomicAdd(&ctrl->n_emptied, 1u);
     }
   }
 }
@@ -868,9 +1361,9 @@ __device__ inline void stored_moments_w(const typename ST::T* B, long long plane
   for (int i = 0; i < Q; ++i) f[i] = ST::ldw(B + i * plane + n);
   density<Q, ST::kShift, R>(f, rho, drho);
   momentum<Q, R>(f, jx, jy, jz);
-  u[0] = jx / rho - (R)0.5 * (R)p.g[0];
-  u[1] = jy / rho - (R)0.5 * (R)p.g[1];
-  u[2] = jz / rho - (R)0.5 * (R)p.g[2];
+  u[0] = jx / rho - (R)0.5 * PAR(R, p, g[0]);
+  u[1] = jy / rho - (R)0.5 * PAR(R, p, g[1]);
+  u[2] = jz / rho - (R)0.5 * PAR(R, p, g[2]);
 }
 
 __device__ __forceinline__ bool valid_src(const uint8_t* flags, int n) {
@@ -984,7 +1477,7 @@ __global__ void __launch_bounds__(128) k_refill(Dev d, Geom g, Phys p) {
             else du[a][b] = (R)0;
           }
         }
-        const R coef = (R)p.geq_coef;
+        const R coef = PAR(R, p, geq_coef);
         const int cc[3] = {rc(li, 0), rc(li, 1), rc(li, 2)};
         R sum = (R)0;
         for (int a = 0; a < 3; ++a)
@@ -1209,7 +1702,7 @@ static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
     }
   }
   __threadfence();
-  if (threadIdx.x == 0) last = atomicAdd(&ctrl->pad[1], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) last = atomicAdd(&ctrl->end_blocks, 1u) == gridDim.x - 1;
   __syncthreads();
   if (!last) return;
   __threadfence();
@@ -1239,13 +1732,14 @@ static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
       ctrl->trace_count += 1;
     }
     ctrl->last[0] = ctrl->n_fill;
-    ctrl->last[1] = ctrl->pad[0];
+    ctrl->last[1] = ctrl->n_emptied;
     ctrl->last[2] = ctrl->n_new;
     ctrl->last[3] = ctrl->n_if;
     ctrl->n_if = ctrl->n_fill = ctrl->n_empty = 0;
     ctrl->n_new = ctrl->n_l2i = ctrl->n_recv = 0;
-    ctrl->pad[0] = 0;
-    ctrl->pad[1] = 0;
+    ctrl->n_emptied = 0;
+    ctrl->end_blocks = 0;
+    ctrl->n_tiles = 0;
     __threadfence();
     ctrl->step += 1;
   }
@@ -1451,7 +1945,9 @@ struct Kernels {
   // the buffer parity is read on the device from the step counter, so the
   // launch sequence is the same for every step (and graph-capturable)
   static cudaError_t step(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
-    stream_collide(d, g, p, s);
+    cudaError_t e = pre_bulk(d, g, p, s);
+    if (e == cudaSuccess) e = stream_collide(d, g, p, s);
+    if (e != cudaSuccess) return e;
     k_stream_collide_if<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
     k_fill<Q><<<kListBlocks, 256, 0, s>>>(d, g);
     k_empty<Q, ST><<<kListBlocks, 256, 0, s>>>(d, g);
@@ -1490,19 +1986,108 @@ struct Kernels {
     k_export_plane<Q, ST><<<4 * 152, 256, 0, s>>>(d, g, cur, i, dst);
     return cudaGetLastError();
   }
+  // resolved bulk-kernel variant of the 16/32-bit path
+  static int variant_of(const Geom& g) {
+    constexpr bool half = sizeof(typename ST::T) == 2;
+    if ((g.variant >= 1 && g.variant <= 4) || g.variant == 6) return g.variant;
+    if ((g.variant == 5 || g.variant == 7) && half) return g.variant;
+    return 2;
+  }
+  static cudaError_t pre_bulk(const Dev& d, const Geom& g, const Phys&, cudaStream_t s) {
+    if constexpr (ST::kShift) {
+      if (variant_of(g) == 4) {
+        const int ntx = (g.nx + kBulkTX - 1) / kBulkTX;
+        const long long ntiles = (long long)ntx * g.ny * g.nz;
+        k_tiles<kBulkTX><<<(unsigned)((ntiles + 7) / 8), 256, 0, s>>>(d, g, ntx);
+        return cudaGetLastError();
+      }
+      if (variant_of(g) == 6) {
+        const int ntx = (g.nx + kWarpTX - 1) / kWarpTX;
+        const long long ntiles = (long long)ntx * g.ny * g.nz;
+        k_tiles<kWarpTX><<<(unsigned)((ntiles + 7) / 8), 256, 0, s>>>(d, g, ntx);
+        return cudaGetLastError();
+      }
+    }
+    return cudaSuccess;
+  }
   static cudaError_t stream_collide(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
     if constexpr (ST::kShift) {
-      dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
-      k_stream_collide_lp<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
+      const int v = variant_of(g);
+      if (v == 4) {
+        // persistent grid: as many CTAs as fit on the GPU (queried once)
+        static int grid = 0;
+        constexpr size_t smem = BulkRing<Q, ST>::bytes;
+        if (grid == 0) {
+          cudaError_t e = cudaFuncSetAttribute(k_stream_collide_bulk<Q, ST>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+          if (e != cudaSuccess) return e;
+          int per_sm = 0, dev = 0, sms = 0;
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_bulk<Q, ST>,
+                                                            kBulkThreads, smem);
+          if (e != cudaSuccess) return e;
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          grid = (per_sm > 0 ? per_sm : 1) * sms;
+        }
+        const int ntx = (g.nx + kBulkTX - 1) / kBulkTX;
+        k_stream_collide_bulk<Q, ST><<<grid, kBulkThreads, smem, s>>>(d, g, p, ntx);
+      } else if (v == 6) {
+        static int grid = 0;
+        constexpr size_t smem = WarpRing<Q, ST>::bytes;
+        if (grid == 0) {
+          cudaError_t e = cudaFuncSetAttribute(k_stream_collide_wtma<Q, ST>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+          if (e != cudaSuccess) return e;
+          int per_sm = 0, dev = 0, sms = 0;
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_wtma<Q, ST>,
+                                                            32 * kWarpsPerBlock, smem);
+          if (e != cudaSuccess) return e;
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          grid = (per_sm > 0 ? per_sm : 1) * sms;
+        }
+        const int ntx = (g.nx + kWarpTX - 1) / kWarpTX;
+        k_stream_collide_wtma<Q, ST><<<grid, 32 * kWarpsPerBlock, smem, s>>>(d, g, p, ntx);
+      } else if (v == 7) {
+        if constexpr (sizeof(typename ST::T) == 2) {
+          // rows split among about 3 blocks per SM x 152 SMs x 2 waves
+          const int tx = (g.nx + 255) / 256;
+          const int nrows = g.ny * g.nz;
+          int G = (152 * 3 * 2 + tx - 1) / tx;
+          if (G > nrows) G = nrows;
+          dim3 b1(128), g1(tx, G, 1);
+          k_stream_collide_pp<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
+        }
+      } else if (v == 5) {
+        if constexpr (sizeof(typename ST::T) == 2) {
+          dim3 b1(64), g1((g.nx + 255) / 256, g.ny, g.nz);
+          k_stream_collide_lp4<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
+        }
+      } else if (v == 1) {
+        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
+        k_stream_collide_lp<Q, ST, 128, 4, true><<<g1, b1, 0, s>>>(d, g, p);
+      } else if (v == 2) {
+        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
+        k_stream_collide_lp<Q, ST, 128, 4, false><<<g1, b1, 0, s>>>(d, g, p);
+      } else {
+        dim3 b1(64), g1((g.nx + 127) / 128, g.ny, g.nz);
+        k_stream_collide_lp<Q, ST, 64, 8, false><<<g1, b1, 0, s>>>(d, g, p);
+      }
     } else {
       dim3 b1(128), g1((g.nx + 127) / 128, g.ny, g.nz);
       k_stream_collide<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
     }
     return cudaGetLastError();
   }
+  static int launches(const Geom& g) {
+    if constexpr (ST::kShift) return (variant_of(g) == 4 || variant_of(g) == 6) ? 12 : 11;
+    return 11;
+  }
   static const Launch* table() {
     static const Launch L = {&step, &init, &total_mass, &max_velocity, &export_pdf,
-                             &stream_collide, 11};
+                             &pre_bulk, &stream_collide, &launches};
     return &L;
   }
 };

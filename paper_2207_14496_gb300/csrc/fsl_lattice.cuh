@@ -134,6 +134,22 @@ struct SF16 {
   static __device__ __forceinline__ void st2(T* p, float a, float b) {
     *reinterpret_cast<__half2*>(p) = __floats2half2_rn(a, b);
   }
+  // the 16 bits that st1 would store
+  static __device__ __forceinline__ unsigned bits(float a) {
+    return (unsigned)__half_as_ushort(__float2half_rn(a));
+  }
+  // two stored values packed in a 32-bit word (low half first) and back
+  static __device__ __forceinline__ float2 unpack2(unsigned w) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return __half22float2(h);
+  }
+  static __device__ __forceinline__ unsigned pack2(float a, float b) {
+    const __half2 h = __floats2half2_rn(a, b);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
+  }
   static __device__ __forceinline__ R ldw(const T* p) { return __half2float(__ldg(p)) * kInv; }
   static __device__ __forceinline__ void stw(T* p, R v) { *p = __float2half_rn(v * kScale); }
   static __device__ __forceinline__ double ldf(const T* p, double w) {
@@ -157,6 +173,20 @@ struct SBF16 {
   static __device__ __forceinline__ void st1(T* p, float a) { *p = __float2bfloat16_rn(a); }
   static __device__ __forceinline__ void st2(T* p, float a, float b) {
     *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(a, b);
+  }
+  static __device__ __forceinline__ unsigned bits(float a) {
+    return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(a));
+  }
+  static __device__ __forceinline__ float2 unpack2(unsigned w) {
+    __nv_bfloat162 h;
+    memcpy(&h, &w, 4);
+    return __bfloat1622float2(h);
+  }
+  static __device__ __forceinline__ unsigned pack2(float a, float b) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    unsigned w;
+    memcpy(&w, &h, 4);
+    return w;
   }
   static __device__ __forceinline__ R ldw(const T* p) { return __bfloat162float(__ldg(p)); }
   static __device__ __forceinline__ void stw(T* p, R v) { *p = __float2bfloat16_rn(v); }

@@ -1,5 +1,12 @@
 """Paper-scale experiments run on the CUDA library.
 
+`dam_break` runs the rectangular dam break of Sec. 4.2 (free-slip walls,
+Smagorinsky model, W in {50, 100, 200}) and reports the residual height and
+front position over time and any instability.
+
+`batched_waves` runs the set of 320 small independent wave domains as one
+batch and as one launch per domain.
+
 `gravity_wave` reproduces the standing gravity wave of Sec. 4.1 at the
 paper's resolutions (L in {200, 400, 800}, omega = 1.8, Re = 10, d = L/2,
 a0 = 0.01 L, D3Q19 SRT) for the five refilling schemes and evaluates the
@@ -40,6 +47,15 @@ def wave_setting(L: int, omega: float = 1.8, re: float = 10.0):
     return dict(nu=nu, k=k, d=d, a0=a0, omega0=w0, g=g)
 
 
+def _smooth(a, k: int = 5):
+    """Centred moving average over k samples (t* = 0.05 at the monitoring
+    interval): removes the one-sample jitter that conversions add."""
+    if len(a) < k:
+        return a
+    pad = np.pad(a, (k // 2, k // 2), mode="edge")
+    return np.convolve(pad, np.ones(k) / k, mode="valid")
+
+
 def _crossings(t, a):
     """Times where a changes sign, linearly interpolated."""
     s = np.sign(a)
@@ -47,20 +63,8 @@ def _crossings(t, a):
     return t[idx] - a[idx] * (t[idx + 1] - t[idx]) / (a[idx + 1] - a[idx])
 
 
-def _maxima(t, a):
-    """Positive local maxima (three-point parabola refinement)."""
-    out = []
-    for i in range(1, len(a) - 1):
-        if a[i] > 0 and a[i] >= a[i - 1] and a[i] > a[i + 1]:
-            y0, y1, y2 = a[i - 1], a[i], a[i + 1]
-            den = y0 - 2 * y1 + y2
-            off = 0.5 * (y0 - y2) / den if den != 0 else 0.0
-            out.append((t[i] + off * (t[i + 1] - t[i]), y1 - 0.25 * (y0 - y2) * off))
-    return out
-
-
 def gravity_wave(L: int, scheme: str, precision: str = "fp64", periods: float = 1.15,
-                 device: int = 0):
+                 device: int = 0, save_trace: str | None = None):
     """Run one wave and evaluate its first half period and first decrement."""
     from . import fsl
     s = wave_setting(L)
@@ -88,29 +92,168 @@ def gravity_wave(L: int, scheme: str, precision: str = "fp64", periods: float = 
     wall = time.perf_counter() - t0
     tr = np.concatenate(trace)
     tstar = (np.arange(len(tr)) + 1) * every * s["omega0"]
-    a = (tr[:, 0] - s["d"]) / s["a0"]
+    a = _smooth((tr[:, 0] - s["d"]) / s["a0"])
     cr = _crossings(tstar, a)
-    # the first positive maximum is the initial elevation at t* = 0
-    mx = [(0.0, a_init)] + _maxima(tstar, a)
     half = float(cr[1] - cr[0]) if len(cr) >= 2 else None
-    dec = float(math.log(mx[0][1] / mx[1][1])) if len(mx) >= 2 and mx[1][1] > 0 else None
+    # first positive maxima: the initial elevation at t* = 0 and the largest
+    # elevation around one period later
+    win = (tstar > 1.5 * math.pi) & (tstar < 2.5 * math.pi)
+    dec = None
+    if win.any() and a[win].max() > 0:
+        dec = float(math.log(a_init / a[win].max()))
     st = sim.status()
     cells = L * L
+    if save_trace:
+        np.save(save_trace, np.stack([tstar, a]))
     return dict(L=L, scheme=scheme, precision=precision, steps=done,
                 half_period=half, log_decrement=dec,
                 first_crossing=float(cr[0]) if len(cr) else None,
                 unstable_step=st[1], seconds=wall, mlups=cells * done / wall / 1e6)
 
 
+def dam_break(W: int, scheme: str, precision: str = "fp64", t_end: float = 3.5,
+              device: int = 0):
+    """The paper's rectangular dam break (Sec. 4.2) with free-slip walls and the
+    Smagorinsky model: residual height h* = h/H at x = 0 and front w* = w/W at
+    y = 0 over t* = t sqrt(2 g / W), sampled every t* = 0.01; the step at which
+    an instability (|u| >= c_s) was latched, if any."""
+    from . import fsl
+    w = inputs.paper_dam_break(W, refill=scheme)
+    sim = fsl.Sim(w["params"], precision, device=device)
+    sim.init_workload(w)
+    rate = math.sqrt(2.0 * w["g"] / W)          # t* per step
+    every = max(1, int(round(0.01 / rate)))
+    steps = int(t_end / rate)
+    sim.set_trace(every)
+    t0 = time.perf_counter()
+    trace = []
+    done = 0
+    while done < steps:
+        k = min(every * 4096, steps - done)
+        k -= k % every
+        if k <= 0:
+            break
+        sim.step(k)
+        done += k
+        trace.append(sim.trace(k // every))
+        sim.set_trace(every)
+    wall = time.perf_counter() - t0
+    tr = np.concatenate(trace)
+    tstar = (np.arange(len(tr)) + 1) * every * rate
+    hstar = tr[:, 2] / w["height"]
+    wstar = tr[:, 1] / W
+    st = sim.status()
+    out = dict(W=W, scheme=scheme, precision=precision, steps=done, seconds=wall,
+               unstable_tstar=(st[1] * rate if st[1] >= 0 else None))
+    for t in (0.5, 1.0, 1.5, 2.0, 2.5, 3.0):
+        i = int(np.searchsorted(tstar, t))
+        if i < len(tstar):
+            out[f"h*@{t}"] = float(hstar[i])
+            out[f"w*@{t}"] = float(wstar[i])
+    return out
+
+
+def batched_waves(steps: int = 4000, n_geom: int = 64, precision: str = "fp16",
+                  chunk: int = 16, tune: bool = True, seed: int = 2207, device: int = 0):
+    """The batched standing-wave set: n_geom geometries (wavelength U[32, 256],
+    width 1..8, depth L/2, amplitude 0.01 L, viscosity U[1e-3, 1e-2],
+    g = 1e-5) times the five refilling schemes, FP16 storage.  Runs `steps`
+    steps (a) with one fsl_step per domain, one after another on a single
+    stream (the per-domain baseline) and (b) as one batch (one graph launch
+    per `chunk` steps, the domains as independent branches) after the
+    variant autotuner; reports both throughputs (all cells) and checks that
+    every domain ends bit-identical in the two runs."""
+    import torch
+
+    from . import autotune, fsl
+    specs = inputs.batched_waves(seed=seed, n_geom=n_geom)
+    ws = [inputs.standing_wave(sp["lam"], nz=sp["width"], nu=sp["nu"], refill=sp["refill"])
+          for sp in specs]
+    cells = sum(w["phi"].size for w in ws)
+
+    def build(stream=None):
+        sims = []
+        for w in ws:
+            s = fsl.Sim(w["params"], precision, device=device, stream=stream)
+            s.init_workload(w)
+            sims.append(s)
+        return sims
+
+    def state(s):
+        t = s.types()
+        fl = (t == 1) | (t == 2)
+        return t, s.pdfs()[:, fl], s.mass()[t == 1]
+
+    out = dict(domains=len(ws), cells=cells, steps=steps, precision=precision, chunk=chunk)
+    # (a) one launch per domain on one stream
+    one = torch.cuda.Stream(device=device)
+    sims = build(one)
+    picks = autotune.tune_batch(sims) if tune else {}
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(one)
+    for s in sims:
+        s.step(steps)
+    e1.record(one)
+    torch.cuda.synchronize()
+    ms_a = e0.elapsed_time(e1)
+    ref = [state(s) for s in sims[:: max(1, len(sims) // 16)]]
+    for s in sims:
+        s.close()
+    del sims
+    torch.cuda.empty_cache()
+    # (b) one batch
+    sims = build()
+    if tune:
+        autotune.tune_batch(sims)
+    stream = torch.cuda.Stream(device=device)
+    b = fsl.Batch(sims, chunk=chunk, stream=stream)
+    b.step(chunk)  # capture and warm the graph outside the timed region
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(steps - chunk)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_b = e0.elapsed_time(e1) * steps / (steps - chunk)
+    got = [state(s) for s in sims[:: max(1, len(sims) // 16)]]
+    same = all(all(np.array_equal(x, y) for x, y in zip(r, g_)) for r, g_ in zip(ref, got))
+    status = [s.status() for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    out.update(per_domain_ms=ms_a, batched_ms=ms_b,
+               per_domain_mlups=cells * steps / (ms_a * 1e3),
+               batched_mlups=cells * steps / (ms_b * 1e3),
+               speedup=ms_a / ms_b, bitwise_equal_sampled=bool(same),
+               unstable=[i for i, st in enumerate(status) if st[0] != 0],
+               variants=sorted({p["variant"] for p in picks.values()}) if picks else None)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--L", type=int, nargs="+", default=[200, 400, 800])
+    ap.add_argument("--L", type=int, nargs="*", default=[200, 400, 800])
     ap.add_argument("--schemes", nargs="+", default=list(inputs.REFILL_SCHEMES))
     ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--save-dir", default=None, help="write each a*(t*) trace as .npy here")
+    ap.add_argument("--dam-break", type=int, nargs="*", default=[],
+                    help="also run the Sec. 4.2 dam break at these column widths W")
+    ap.add_argument("--batched", type=int, default=0,
+                    help="also run the batched standing-wave set for this many steps")
     args = ap.parse_args()
+    if args.batched:
+        print(json.dumps(batched_waves(steps=args.batched)), flush=True)
+    for W in args.dam_break:
+        for sc in args.schemes:
+            print(json.dumps(dam_break(W, sc, args.precision)), flush=True)
     for L in args.L:
         for sc in args.schemes:
-            r = gravity_wave(L, sc, args.precision)
+            path = None
+            if args.save_dir:
+                import os
+                os.makedirs(args.save_dir, exist_ok=True)
+                path = os.path.join(args.save_dir, f"wave_L{L}_{sc}_{args.precision}.npy")
+            r = gravity_wave(L, sc, args.precision, save_trace=path)
             r["paper_L800"] = dict(half_period=PAPER_L800["half_period"].get(sc),
                                    log_decrement=PAPER_L800["log_decrement"].get(sc))
             print(json.dumps(r), flush=True)

@@ -57,6 +57,8 @@ class fsl_config(ctypes.Structure):
         ("p_volume", ctypes.c_double),
         ("eps_phi", ctypes.c_double),
         ("options", ctypes.c_uint),
+        ("les_cs", ctypes.c_double),
+        ("free_slip", ctypes.c_int * 3),
     ]
 
 
@@ -78,8 +80,18 @@ _lib.fsl_launches_per_step.argtypes = [_VP]
 _lib.fsl_launches_per_step.restype = ctypes.c_int
 _lib.fsl_kernel_stats.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP]
 _lib.fsl_kernel_stats.restype = ctypes.c_int
+_lib.fsl_set_variant.argtypes = [_VP, ctypes.c_int]
+_lib.fsl_set_variant.restype = ctypes.c_int
+_lib.fsl_get_variant.argtypes = [_VP]
+_lib.fsl_get_variant.restype = ctypes.c_int
 _lib.fsl_total_mass_noalloc.argtypes = [ctypes.POINTER(fsl_config), _VP, _VP, _VP, _VP, _VP, _VP]
 _lib.fsl_total_mass_noalloc.restype = ctypes.c_int
+_lib.fsl_batch_create.argtypes = [_VP, ctypes.c_int, _VP, ctypes.c_int, ctypes.POINTER(_VP)]
+_lib.fsl_batch_create.restype = ctypes.c_int
+_lib.fsl_batch_step.argtypes = [_VP, ctypes.c_int]
+_lib.fsl_batch_step.restype = ctypes.c_int
+_lib.fsl_batch_destroy.argtypes = [_VP]
+_lib.fsl_batch_destroy.restype = ctypes.c_int
 _lib.fsl_status_string.argtypes = [ctypes.c_int]
 _lib.fsl_status_string.restype = ctypes.c_char_p
 _lib.fsl_last_error.restype = ctypes.c_char_p
@@ -91,8 +103,12 @@ for _name in ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", 
 EXPORTED = ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "fsl_observe",
             "fsl_set_trace", "fsl_trace_capacity", "fsl_state_bytes", "fsl_save", "fsl_load",
             "fsl_destroy", "fsl_lattice_table", "fsl_launches_per_step", "fsl_kernel_stats",
-            "fsl_status_string", "fsl_last_error", "fsl_total_mass_noalloc")
+            "fsl_status_string", "fsl_last_error", "fsl_total_mass_noalloc", "fsl_set_variant",
+            "fsl_get_variant", "fsl_batch_create", "fsl_batch_step", "fsl_batch_destroy")
+VARIANTS = {"default": 0, "pair": 1, "pair_r128": 2, "pair64_r128": 3, "tma": 4, "quad64": 5, "warp_tma": 6,
+            "pair_pipe": 7}
 KERNEL_STREAM_COLLIDE = 1
+KERNEL_BULK_PASS = 2
 
 
 class FslError(RuntimeError):
@@ -129,6 +145,10 @@ def make_config(params: dict, precision: str = "fp64") -> fsl_config:
     c.p_volume = float(params.get("p_v", 1.0 / 3.0))
     c.eps_phi = float(params.get("eps", 1e-2))
     c.options = int(params.get("options", 0))
+    c.les_cs = float(params.get("les_cs", 0.0))
+    fs = params.get("free_slip", (False, False, False))
+    for a in range(3):
+        c.free_slip[a] = 1 if fs[a] else 0
     return c
 
 
@@ -192,6 +212,13 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+    def set_variant(self, variant):
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        _check(_lib.fsl_set_variant(self.h, v), "fsl_set_variant")
+
+    def variant(self) -> int:
+        return int(_lib.fsl_get_variant(self.h))
 
     def launches_per_step(self) -> int:
         return int(_lib.fsl_launches_per_step(self.h))
@@ -300,6 +327,41 @@ class Sim:
     def load(self, buf: np.ndarray):
         buf = np.ascontiguousarray(buf, dtype=np.uint8)
         _check(_lib.fsl_load(self.h, _ptr(buf), buf.nbytes), "fsl_load")
+
+
+class Batch:
+    """Many independent simulations stepped together: one CUDA-graph launch
+    per `chunk` steps, each member an independent branch of the graph.  The
+    members keep their own state and stay usable (observe, save, load)."""
+
+    def __init__(self, sims, chunk: int = 8, stream=None):
+        import torch
+
+        self.sims = list(sims)
+        if not self.sims:
+            raise ValueError("a batch needs at least one simulation")
+        dev = self.sims[0].device
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        arr = (_VP * len(self.sims))(*[s.h.value for s in self.sims])
+        b = ctypes.c_void_p()
+        _check(_lib.fsl_batch_create(ctypes.cast(arr, _VP), len(self.sims),
+                                     ctypes.c_void_p(self.stream.cuda_stream), int(chunk),
+                                     ctypes.byref(b)), "fsl_batch_create")
+        self.b = b
+
+    def step(self, n: int = 1):
+        _check(_lib.fsl_batch_step(self.b, int(n)), "fsl_batch_step")
+
+    def close(self):
+        if getattr(self, "b", None) is not None and self.b.value:
+            _lib.fsl_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def raw_library():

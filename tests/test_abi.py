@@ -74,3 +74,19 @@ def test_lattice_table(lib, q):
         assert w[i] == pub[int(l2[i])]
     assert abs(w.sum() - 1) < 1e-15
     assert np.allclose(np.einsum("i,ia,ib->ab", w, c, c), np.eye(3) / 3)
+
+
+def test_batch_create_rejects_bad_arguments():
+    """Argument checks of fsl_batch_create run before any CUDA call."""
+    import ctypes
+    from paper_2207_14496_gb300 import fsl
+    lib = fsl.raw_library()
+    out = ctypes.c_void_p()
+    assert lib.fsl_batch_create(None, 1, ctypes.c_void_p(1), 8, ctypes.byref(out)) == -1
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.fsl_batch_create(ctypes.cast(arr, ctypes.c_void_p), 1, ctypes.c_void_p(1), 8,
+                                ctypes.byref(out)) == -1
+    assert lib.fsl_batch_create(ctypes.cast(arr, ctypes.c_void_p), 0, ctypes.c_void_p(1), 8,
+                                ctypes.byref(out)) == -1
+    assert lib.fsl_batch_step(None, 1) == -1
+    assert lib.fsl_batch_destroy(None) == -1

@@ -129,3 +129,26 @@ def test_drop_impact_256_full_size_sampled(fsl):
     sim.step(2)
     orc.step(2)
     compare_state(sim, orc, 2, RTOL, label="drop256")
+
+
+@pytest.mark.parametrize("scheme", inputs.REFILL_SCHEMES)
+def test_free_slip_les_dam_break(fsl, scheme):
+    """The paper's dam-break walls and turbulence model (Sec. 4.2): free-slip
+    walls on x and y (specular reflection, mirrored mass flux), Smagorinsky
+    C_S = 0.1, D3Q19 TRT, 2D (periodic z, nz = 1), every refilling scheme."""
+    w = inputs.dam_break(nx=90, ny=50, nz=1, width=20, height=30, g=2e-4, nu=2e-3,
+                         refill=scheme)
+    w["params"]["periodic"] = (False, False, True)
+    w["params"]["free_slip"] = (True, True, False)
+    w["params"]["les_cs"] = 0.1
+    sim, orc, stats, conv = run_parity(fsl, w, 300, 100, RTOL, f"freeslip/{scheme}")
+    assert conv > 50
+
+
+def test_free_slip_3d_mixed_walls_d3q27(fsl):
+    """3D: free-slip x walls, no-slip y and z walls (mixed edges and corners
+    fall back to bounce-back), D3Q27 with LES."""
+    w = inputs.dam_break(nx=40, ny=30, nz=12, width=12, height=18, g=2e-4, nu=3e-3, q=27)
+    w["params"]["free_slip"] = (True, False, False)
+    w["params"]["les_cs"] = 0.1
+    run_parity(fsl, w, 120, 60, RTOL, "freeslip3d")

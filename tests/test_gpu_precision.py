@@ -156,7 +156,7 @@ def test_graph_and_direct_launch_agree(fsl):
     assert np.array_equal(s1.pdfs()[:, fl], s2.pdfs()[:, fl])
 
 
-@pytest.mark.parametrize("case", ["wave64", "wave_wide", "dam", "drop"])
+@pytest.mark.parametrize("case", ["wave64", "wave_wide", "dam", "drop", "freeslip_les"])
 def test_fp32_tracks_fp64_cell_by_cell(fsl, case):
     """FP32 storage and arithmetic must stay within FP32 round-off of the FP64
     path over a short run on every geometry class: one x tile (64 cells),
@@ -169,9 +169,14 @@ def test_fp32_tracks_fp64_cell_by_cell(fsl, case):
         w = inputs.standing_wave(600, ny=40, depth=20.0, amp=2.0, nu=0.02)
     elif case == "dam":
         w = inputs.dam_break(nx=100, ny=48, nz=4, width=24, height=24, g=2e-4, nu=5e-3)
-    else:
+    elif case == "drop":
         w = inputs.drop_impact(n=40, pool=14, diameter=12.0, gap=9.0, speed=0.05, sigma=2e-3,
                                g=1e-5, nu=5e-3, nxy=36)
+    else:
+        w = inputs.dam_break(nx=90, ny=50, nz=1, width=20, height=30, g=2e-4, nu=2e-3)
+        w["params"]["periodic"] = (False, False, True)
+        w["params"]["free_slip"] = (True, True, False)
+        w["params"]["les_cs"] = 0.1
     a = fsl.Sim(w["params"], "fp64")
     b = fsl.Sim(w["params"], "fp32")
     for s in (a, b):
