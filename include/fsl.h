@@ -173,12 +173,13 @@ int fsl_launches_per_step(const fsl_handle* h);
  * in packed FP32 and give identical results (same explicitly rounded
  * arithmetic on the same inputs); they differ in how the stored values reach
  * the registers:
- *   PAIR, PAIR_R128: two cells per thread, 128 threads per block (tiles of
- *     256 cells along x), one aligned 2-value load per direction, values
- *     pulled from x -/+ 1 exchanged between lanes by warp shuffles; PAIR lets
- *     the compiler use as many registers as it likes, PAIR_R128 caps them at
- *     128 (four blocks per SM);
- *   PAIR64_R128: as PAIR_R128 with 64-thread blocks;
+ *   PAIR, PAIR_R96, PAIR_R80, PAIR_R128: two cells per thread, 128 threads
+ *     per block (tiles of 256 cells along x), one aligned 2-value load per
+ *     direction, values pulled from x -/+ 1 exchanged between lanes by warp
+ *     shuffles.  PAIR, PAIR_R96 and PAIR_R80 collide both cells together in
+ *     packed FP32 with at most 128, 96 and 80 registers per thread (four,
+ *     five and six blocks per SM); PAIR_R128 collides them one after the
+ *     other (128 registers);
  *   TMA: persistent, tiles of 256 cells with liquid (listed by a pre-pass)
  *     staged in shared memory by bulk copies through a ring of
  *     mbarrier-guarded stages, one producer warp and four consumer warps;
@@ -195,8 +196,8 @@ int fsl_launches_per_step(const fsl_handle* h);
  * fsl_set_variant drops captured step graphs; FSL_ERR_ARG for an unknown
  * variant and for QUAD_64 or PAIR_PIPE with FP32 storage. */
 enum { FSL_VARIANT_DEFAULT = 0, FSL_VARIANT_PAIR = 1, FSL_VARIANT_PAIR_R128 = 2,
-       FSL_VARIANT_PAIR64_R128 = 3, FSL_VARIANT_TMA = 4, FSL_VARIANT_QUAD_64 = 5,
-       FSL_VARIANT_WARP_TMA = 6, FSL_VARIANT_PAIR_PIPE = 7 };
+       FSL_VARIANT_PAIR_R96 = 3, FSL_VARIANT_TMA = 4, FSL_VARIANT_QUAD_64 = 5,
+       FSL_VARIANT_WARP_TMA = 6, FSL_VARIANT_PAIR_PIPE = 7, FSL_VARIANT_PAIR_R80 = 8 };
 fsl_status fsl_set_variant(fsl_handle* h, int variant);
 int fsl_get_variant(const fsl_handle* h);
 
@@ -267,6 +268,46 @@ fsl_status fsl_batch_create(fsl_handle* const* handles, int n, void* cuda_stream
                             fsl_batch** out);
 fsl_status fsl_batch_step(fsl_batch* b, int nsteps);
 fsl_status fsl_batch_destroy(fsl_batch* b);
+
+/* Discrete adjoint of the step, for gradients of a misfit of the surface
+ * elevation (Sec. 4.1's observable: the column height sum_y phi(0, y, z),
+ * averaged over z) with respect to the viscosity, the gravity and the
+ * initial state.  The paper has no adjoint; this is the differentiation
+ * pattern built around its method.  Scope: FP64 or FP32 storage, SRT, EQ
+ * refilling, no surface tension, no turbulence model, no-slip walls or
+ * periodic faces, no interior obstacles (FSL_ERR_ARG otherwise).  Cell types
+ * and every conversion decision of the forward run are replayed, so the
+ * gradient is that of the step map with those decisions fixed (the usual
+ * discrete adjoint of a free-surface scheme); the stream-collide, the
+ * free-surface boundary condition, the interface mass flux, the fill-level
+ * update, the excess-mass redistribution and the EQ refilling are
+ * differentiated by hand-written kernels.
+ *   fsl_adjoint_workspace_bytes: device bytes for `nsteps` steps with a
+ *     checkpoint every `every` steps (1 <= nsteps <= fsl_trace_capacity());
+ *     memory grows with nsteps / every whole-state copies plus every + 1
+ *     recorded levels;
+ *   fsl_adjoint_create: binds the adjoint to an initialised handle; the
+ *     caller owns the 256-byte-aligned device workspace (released after
+ *     fsl_adjoint_destroy); the adjoint runs on the handle's stream;
+ *   fsl_adjoint_forward: advances the handle by nsteps from its current
+ *     state (time level 0) and writes the column height after each step to
+ *     column (host, nsteps doubles); checkpoints whole states on the device;
+ *   fsl_adjoint_backward: given dJ/dcolumn(t) for t = 1..nsteps (host,
+ *     nsteps doubles) writes out (host, 4 + 2 nx ny nz doubles): dJ/dnu,
+ *     dJ/dg_x, dJ/dg_y, dJ/dg_z (the gravity's direct effect and its effect
+ *     through the hydrostatic initial density of fsl_init_fill), then
+ *     dJ/drho0 and dJ/dphi0 per cell of the level-0 state (dense, x fastest;
+ *     rho0 the initial density, phi0 the initial fill level of interface
+ *     cells).  Replays each segment from its checkpoint; leaves the handle at
+ *     the end of the forward pass.  FSL_ERR_STATE before a forward pass.
+ * Synchronous (they synchronise the handle's stream). */
+typedef struct fsl_adjoint fsl_adjoint;
+fsl_status fsl_adjoint_workspace_bytes(const fsl_handle* h, int nsteps, int every, size_t* bytes);
+fsl_status fsl_adjoint_create(fsl_handle* h, int nsteps, int every, void* d_workspace,
+                              size_t bytes, fsl_adjoint** out);
+fsl_status fsl_adjoint_forward(fsl_adjoint* a, double* column);
+fsl_status fsl_adjoint_backward(fsl_adjoint* a, const double* dj_dcolumn, double* out);
+fsl_status fsl_adjoint_destroy(fsl_adjoint* a);
 
 /* Static description of a status code; last CUDA error text of this thread. */
 const char* fsl_status_string(fsl_status s);

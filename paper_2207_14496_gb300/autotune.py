@@ -20,7 +20,7 @@ import os
 
 from . import fsl
 
-CANDIDATES = ("pair", "pair_r128", "pair64_r128", "tma", "quad64", "warp_tma", "pair_pipe")
+CANDIDATES = ("pair", "pair_r128", "pair_r96", "pair_r80", "tma", "quad64", "warp_tma", "pair_pipe")
 HALF_ONLY = ("quad64", "pair_pipe")
 
 

@@ -2,6 +2,7 @@
 // workspace carving, initial state, step launches (captured into CUDA graphs),
 // observation, checkpointing.  No device memory is allocated here; every
 // device buffer is carved out of the caller's workspace.
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -11,6 +12,7 @@
 
 #include "fsl.h"
 #include "fsl_kernels.cuh"
+#include "fsl_adjoint.cuh"
 
 using namespace fsl;
 
@@ -29,6 +31,8 @@ fsl_status cuda_fail(cudaError_t e, const char* what) {
   } while (0)
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+constexpr long long kPlaneSkew = 512;  // elements added to every PDF plane
 
 enum Region {
   R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST,
@@ -51,7 +55,7 @@ bool valid_config(const fsl_config* c) {
   if (!(c->les_cs >= 0.0) || !std::isfinite(c->les_cs)) return false;
   const long long sx = ((long long)c->nx + 31) / 32 * 32;
   const long long cells = sx * c->ny * (long long)c->nz;
-  const long long plane = (cells + 127) / 128 * 128;
+  const long long plane = (cells + 127) / 128 * 128 + kPlaneSkew;
   if (plane * (long long)c->lattice >= (1ll << 31) * 8ll) return false;
   if (cells >= (1ll << 31) - 1) return false;
   return true;
@@ -63,7 +67,10 @@ void make_geom(const fsl_config* c, Geom* g) {
   g->nz = c->nz;
   g->sx = (c->nx + 31) / 32 * 32;
   g->cells = (long long)g->sx * c->ny * c->nz;
-  g->plane = (g->cells + 127) / 128 * 128;
+  // planes padded to 128 elements plus a skew, so that the q planes (which a
+  // warp streams from at once) do not start at multiples of a large power of
+  // two from each other and spread over the HBM channels
+  g->plane = (g->cells + 127) / 128 * 128 + kPlaneSkew;
   for (int a = 0; a < 3; ++a) g->periodic[a] = c->periodic[a] ? 1 : 0;
   g->has_obst = 0;
   g->variant = FSL_VARIANT_DEFAULT;
@@ -236,6 +243,8 @@ struct fsl_handle {
   int trace_every;
   std::map<int, cudaGraphExec_t> graphs;
   unsigned gen = 0;  // bumped whenever captured launch parameters may change
+  char* base = nullptr;         // start of the workspace
+  double h_ref = 0.0;           // hydrostatic reference height of the last fsl_init_fill
 };
 
 namespace {
@@ -289,6 +298,7 @@ fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, vo
     return FSL_ERR_WORKSPACE;
   }
   char* base = static_cast<char*>(d_workspace);
+  h->base = base;
   Dev& d = h->d;
   d.pdf[0] = base + h->off[R_PDF0];
   d.pdf[1] = base + h->off[R_PDF1];
@@ -343,6 +353,7 @@ fsl_status fsl_init_fill(fsl_handle* h, const double* phi, const double* u0,
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   ++h->gen;
+  h->h_ref = h_ref;
   FSL_CK(h->L->init(h->d, h->g, h->p, 0, su, obstacle ? 1 : 0, h_ref, h->stream));
   k_set_trace<<<1, 32, 0, h->stream>>>(h->d.ctrl, h->trace_every);
   FSL_CK(cudaGetLastError());
@@ -596,6 +607,286 @@ fsl_status fsl_destroy(fsl_handle* h) {
   return FSL_OK;
 }
 
+// ---------------------------------------------------------------- adjoint
+struct fsl_adjoint {
+  fsl_handle* h = nullptr;
+  int nsteps = 0, every = 0, nseg = 0;
+  long long step0 = 0;  // step counter of the handle when the forward pass started
+  size_t fbytes = 0, cells = 0;
+  char* ckpt = nullptr;    // nseg + 1 workspace copies
+  char* tF = nullptr;      // every + 1 levels of stored PDFs
+  uint8_t* tFl = nullptr;  // every + 1 levels of flags
+  double* tM = nullptr;    // every + 1 levels of mass
+  double* tP = nullptr;    // every + 1 levels of fill level
+  char* fld = nullptr;     // adjoint fields
+  double* acc = nullptr;   // 8 accumulators
+  double* dinit = nullptr; // 2 x dense cells: d J / d rho0, d J / d phi0
+  std::vector<double> column;
+  bool forward_done = false;
+};
+
+extern "C++" {
+namespace {
+
+bool adjoint_supported(const fsl_handle* h) {
+  const fsl_config& c = h->cfg;
+  return (c.precision == FSL_FP64 || c.precision == FSL_FP32) && c.collision == FSL_SRT &&
+         c.refill == FSL_REFILL_EQ && c.sigma == 0.0 && c.les_cs == 0.0 && h->g.free_slip == 0 &&
+         h->g.has_obst == 0;
+}
+
+size_t adjoint_layout(const fsl_handle* h, int nsteps, int every, size_t* off) {
+  const int nseg = (nsteps + every - 1) / every;
+  const size_t sb = storage_bytes(h->cfg.precision);
+  const size_t rb = h->cfg.precision == FSL_FP64 ? 8 : 4;
+  const size_t cells = (size_t)h->g.cells;
+  const size_t fbytes = (size_t)h->cfg.lattice * (size_t)h->g.plane * sb;
+  const size_t dense = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  size_t sz[8];
+  sz[0] = (size_t)(nseg + 1) * align256(h->bytes);
+  sz[1] = (size_t)(every + 1) * align256(fbytes);
+  sz[2] = (size_t)(every + 1) * align256(cells);
+  sz[3] = (size_t)(every + 1) * align256(cells * 8);
+  sz[4] = (size_t)(every + 1) * align256(cells * 8);
+  // fields: 4 q-plane arrays (lF, lF0, lfin, spare) + 10 cell arrays + 4 + 3 per cell
+  sz[5] = align256(rb * (4 * (size_t)h->cfg.lattice * h->g.plane + 17 * cells));
+  sz[6] = 256;
+  sz[7] = align256(2 * dense * 8);
+  size_t total = 0;
+  for (int k = 0; k < 8; ++k) {
+    if (off) off[k] = total;
+    total += align256(sz[k]);
+  }
+  return total;
+}
+
+template <class R>
+AdjFields<R> adjoint_fields(fsl_adjoint* a) {
+  const fsl_handle* h = a->h;
+  const size_t qp = (size_t)h->cfg.lattice * h->g.plane, n = (size_t)h->g.cells;
+  R* b = reinterpret_cast<R*>(a->fld);
+  AdjFields<R> f;
+  f.lF = b;
+  f.lF0 = b + qp;
+  f.lfin = b + 2 * qp;
+  R* cb = b + 4 * qp;
+  f.lM = cb;
+  f.lM0 = cb + n;
+  f.lP = cb + 2 * n;
+  f.lP0 = cb + 3 * n;
+  f.lm1 = cb + 4 * n;
+  f.lrhoP = cb + 5 * n;
+  f.lmnew = cb + 6 * n;
+  f.lrho = cb + 7 * n;
+  f.lbar = cb + 10 * n;  // 4 per cell
+  f.lg = cb + 14 * n;    // 3 per cell
+  f.acc = a->acc;
+  return f;
+}
+
+// copy the handle's current state into tape level j
+fsl_status adjoint_record(fsl_adjoint* a, int j, long long step) {
+  fsl_handle* h = a->h;
+  const int cur = (int)(step & 1);
+  FSL_CK(cudaMemcpyAsync(a->tF + (size_t)j * align256(a->fbytes), h->d.pdf[cur], a->fbytes,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  FSL_CK(cudaMemcpyAsync(a->tFl + (size_t)j * align256(a->cells), h->d.flags, a->cells,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  FSL_CK(cudaMemcpyAsync(a->tM + (size_t)j * align256(a->cells * 8) / 8, h->d.mass, a->cells * 8,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  FSL_CK(cudaMemcpyAsync(a->tP + (size_t)j * align256(a->cells * 8) / 8, h->d.phi, a->cells * 8,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  return FSL_OK;
+}
+
+AdjLevel adjoint_level(const fsl_adjoint* a, int j) {
+  AdjLevel L;
+  L.F = a->tF + (size_t)j * align256(a->fbytes);
+  L.flags = a->tFl + (size_t)j * align256(a->cells);
+  L.M = a->tM + (size_t)j * align256(a->cells * 8) / 8;
+  L.Phi = a->tP + (size_t)j * align256(a->cells * 8) / 8;
+  return L;
+}
+
+template <int Q, class ST>
+fsl_status adjoint_step(fsl_adjoint* a, const AdjLevel& L0, const AdjLevel& L1) {
+  using R = typename ST::R;
+  fsl_handle* h = a->h;
+  AdjFields<R> f = adjoint_fields<R>(a);
+  const int blocks = (int)((a->cells + 255) / 256);
+  k_adj_phi<Q, ST><<<blocks, 256, 0, h->stream>>>(h->g, h->p, L0, L1, f);
+  k_adj_mass<Q, ST><<<blocks, 256, 0, h->stream>>>(h->g, h->p, L0, L1, f);
+  k_adj_refill<Q, ST><<<blocks, 256, 0, h->stream>>>(h->g, h->p, L0, L1, f);
+  k_adj_collide<Q, ST><<<blocks, 256, 0, h->stream>>>(h->g, h->p, L0, L1, f);
+  k_adj_state<Q, ST><<<blocks, 256, 0, h->stream>>>(h->g, h->p, L0, f);
+  FSL_CK(cudaGetLastError());
+  // the level-t adjoint becomes the input of the next (earlier) step
+  const size_t rb = sizeof(R);
+  const size_t qp = (size_t)h->cfg.lattice * h->g.plane;
+  FSL_CK(cudaMemcpyAsync(f.lF, f.lF0, qp * rb, cudaMemcpyDeviceToDevice, h->stream));
+  FSL_CK(cudaMemcpyAsync(f.lM, f.lM0, a->cells * rb, cudaMemcpyDeviceToDevice, h->stream));
+  FSL_CK(cudaMemcpyAsync(f.lP, f.lP0, a->cells * rb, cudaMemcpyDeviceToDevice, h->stream));
+  return FSL_OK;
+}
+
+template <int Q, class ST>
+fsl_status adjoint_init(fsl_adjoint* a, const AdjLevel& L0) {
+  using R = typename ST::R;
+  fsl_handle* h = a->h;
+  AdjFields<R> f = adjoint_fields<R>(a);
+  const size_t dense = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  k_adj_init<Q, ST><<<(unsigned)((a->cells + 255) / 256), 256, 0, h->stream>>>(
+      h->g, h->p, L0, f, h->h_ref, a->dinit, a->dinit + dense);
+  FSL_CK(cudaGetLastError());
+  return FSL_OK;
+}
+
+fsl_status adjoint_dispatch_step(fsl_adjoint* a, const AdjLevel& L0, const AdjLevel& L1) {
+  const int q = a->h->cfg.lattice;
+  if (a->h->cfg.precision == FSL_FP64)
+    return q == 19 ? adjoint_step<19, SF64>(a, L0, L1) : adjoint_step<27, SF64>(a, L0, L1);
+  return q == 19 ? adjoint_step<19, SF32>(a, L0, L1) : adjoint_step<27, SF32>(a, L0, L1);
+}
+
+fsl_status adjoint_dispatch_init(fsl_adjoint* a, const AdjLevel& L0) {
+  const int q = a->h->cfg.lattice;
+  if (a->h->cfg.precision == FSL_FP64)
+    return q == 19 ? adjoint_init<19, SF64>(a, L0) : adjoint_init<27, SF64>(a, L0);
+  return q == 19 ? adjoint_init<19, SF32>(a, L0) : adjoint_init<27, SF32>(a, L0);
+}
+
+}  // namespace
+}  // extern "C++"
+
+fsl_status fsl_adjoint_workspace_bytes(const fsl_handle* h, int nsteps, int every, size_t* bytes) {
+  if (!h || !bytes || nsteps < 1 || every < 1 || nsteps > kTraceCapacity) return FSL_ERR_ARG;
+  if (!adjoint_supported(h)) return FSL_ERR_ARG;
+  *bytes = adjoint_layout(h, nsteps, every, nullptr);
+  return FSL_OK;
+}
+
+fsl_status fsl_adjoint_create(fsl_handle* h, int nsteps, int every, void* d_workspace,
+                              size_t bytes, fsl_adjoint** out) {
+  if (!h || !out || nsteps < 1 || every < 1 || nsteps > kTraceCapacity) return FSL_ERR_ARG;
+  if (!adjoint_supported(h) || !h->ready) return FSL_ERR_ARG;
+  if (!d_workspace || (reinterpret_cast<uintptr_t>(d_workspace) & 255u)) return FSL_ERR_WORKSPACE;
+  size_t off[8];
+  if (bytes < adjoint_layout(h, nsteps, every, off)) return FSL_ERR_WORKSPACE;
+  fsl_adjoint* a = new fsl_adjoint;
+  a->h = h;
+  a->nsteps = nsteps;
+  a->every = every;
+  a->nseg = (nsteps + every - 1) / every;
+  a->cells = (size_t)h->g.cells;
+  a->fbytes = (size_t)h->cfg.lattice * (size_t)h->g.plane * storage_bytes(h->cfg.precision);
+  char* b = static_cast<char*>(d_workspace);
+  a->ckpt = b + off[0];
+  a->tF = b + off[1];
+  a->tFl = reinterpret_cast<uint8_t*>(b + off[2]);
+  a->tM = reinterpret_cast<double*>(b + off[3]);
+  a->tP = reinterpret_cast<double*>(b + off[4]);
+  a->fld = b + off[5];
+  a->acc = reinterpret_cast<double*>(b + off[6]);
+  a->dinit = reinterpret_cast<double*>(b + off[7]);
+  *out = a;
+  return FSL_OK;
+}
+
+fsl_status fsl_adjoint_forward(fsl_adjoint* a, double* column) {
+  if (!a || !column) return FSL_ERR_ARG;
+  fsl_handle* h = a->h;
+  Ctrl c;
+  fsl_status st = read_ctrl(h, &c);
+  if (st != FSL_OK) return st;
+  a->step0 = c.step;
+  const int saved_every = h->trace_every;
+  st = fsl_set_trace(h, 1);
+  if (st != FSL_OK) return st;
+  const size_t wb = align256(h->bytes);
+  for (int k = 0; k < a->nseg; ++k) {
+    FSL_CK(cudaMemcpyAsync(a->ckpt + (size_t)k * wb, h->base, h->bytes, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    const int len = std::min(a->every, a->nsteps - k * a->every);
+    st = fsl_step(h, len);
+    if (st != FSL_OK) return st;
+  }
+  FSL_CK(cudaMemcpyAsync(a->ckpt + (size_t)a->nseg * wb, h->base, h->bytes,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  std::vector<double> tr((size_t)a->nsteps * 3);
+  st = fsl_observe(h, FSL_OBS_TRACE, tr.data(), tr.size() * sizeof(double));
+  if (st != FSL_OK) return st;
+  a->column.resize(a->nsteps);
+  for (int t = 0; t < a->nsteps; ++t) a->column[t] = column[t] = tr[3 * (size_t)t];
+  // the final state keeps the trace setting the caller had
+  h->trace_every = saved_every;
+  k_set_trace<<<1, 32, 0, h->stream>>>(h->d.ctrl, saved_every);
+  FSL_CK(cudaGetLastError());
+  FSL_CK(cudaMemcpyAsync(a->ckpt + (size_t)a->nseg * wb, h->base, h->bytes,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  a->forward_done = true;
+  return FSL_OK;
+}
+
+fsl_status fsl_adjoint_backward(fsl_adjoint* a, const double* dj_dcolumn, double* out) {
+  if (!a || !dj_dcolumn || !out) return FSL_ERR_ARG;
+  if (!a->forward_done) return FSL_ERR_STATE;
+  fsl_handle* h = a->h;
+  const size_t wb = align256(h->bytes);
+  const size_t rb = h->cfg.precision == FSL_FP64 ? 8 : 4;
+  const size_t qp = (size_t)h->cfg.lattice * h->g.plane;
+  const size_t dense = (size_t)h->g.nx * h->g.ny * h->g.nz;
+  FSL_CK(cudaMemsetAsync(a->fld, 0, rb * (4 * qp + 17 * a->cells), h->stream));
+  FSL_CK(cudaMemsetAsync(a->acc, 0, 8 * sizeof(double), h->stream));
+  double* lP_dbl = rb == 8 ? reinterpret_cast<double*>(a->fld) + 4 * qp + 2 * a->cells : nullptr;
+  float* lP_flt = rb == 4 ? reinterpret_cast<float*>(a->fld) + 4 * qp + 2 * a->cells : nullptr;
+  for (int k = a->nseg - 1; k >= 0; --k) {
+    const int t0 = k * a->every;
+    const int len = std::min(a->every, a->nsteps - t0);
+    // replay the segment from its checkpoint, recording every level
+    FSL_CK(cudaMemcpyAsync(h->base, a->ckpt + (size_t)k * wb, h->bytes, cudaMemcpyDeviceToDevice,
+                           h->stream));
+    fsl_status st = adjoint_record(a, 0, a->step0 + t0);
+    if (st != FSL_OK) return st;
+    for (int j = 1; j <= len; ++j) {
+      st = fsl_step(h, 1);
+      if (st != FSL_OK) return st;
+      st = adjoint_record(a, j, a->step0 + t0 + j);
+      if (st != FSL_OK) return st;
+    }
+    for (int j = len; j >= 1; --j) {
+      k_adj_observe<<<(h->g.ny * h->g.nz + 255) / 256, 256, 0, h->stream>>>(
+          h->g, dj_dcolumn[t0 + j - 1], lP_dbl, lP_flt);
+      FSL_CK(cudaGetLastError());
+      st = adjoint_dispatch_step(a, adjoint_level(a, j - 1), adjoint_level(a, j));
+      if (st != FSL_OK) return st;
+    }
+  }
+  // level 0 of the first segment is the initial state
+  fsl_status st = adjoint_dispatch_init(a, adjoint_level(a, 0));
+  if (st != FSL_OK) return st;
+  double acc[4];
+  FSL_CK(cudaMemcpyAsync(acc, a->acc, sizeof(acc), cudaMemcpyDeviceToHost, h->stream));
+  FSL_CK(cudaMemcpyAsync(out + 4, a->dinit, 2 * dense * sizeof(double), cudaMemcpyDeviceToHost,
+                         h->stream));
+  // leave the handle at the end of the forward pass
+  FSL_CK(cudaMemcpyAsync(h->base, a->ckpt + (size_t)a->nseg * wb, h->bytes,
+                         cudaMemcpyDeviceToDevice, h->stream));
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  // omega = 1 / (3 nu + 1/2): d omega / d nu = -3 omega^2
+  out[0] = acc[0] * (-3.0 * h->p.omega * h->p.omega);
+  out[1] = acc[1];
+  out[2] = acc[2];
+  out[3] = acc[3];
+  return FSL_OK;
+}
+
+fsl_status fsl_adjoint_destroy(fsl_adjoint* a) {
+  if (!a) return FSL_ERR_ARG;
+  delete a;
+  return FSL_OK;
+}
+
 // ------------------------------------------------------------------ batch
 struct fsl_batch {
   std::vector<fsl_handle*> hs;
@@ -735,7 +1026,7 @@ fsl_status fsl_lattice_table(int lattice, int* c3q, double* w) {
 int fsl_launches_per_step(const fsl_handle* h) { return h ? h->L->launches_per_step(h->g) : 0; }
 
 fsl_status fsl_set_variant(fsl_handle* h, int variant) {
-  if (!h || variant < FSL_VARIANT_DEFAULT || variant > FSL_VARIANT_PAIR_PIPE) return FSL_ERR_ARG;
+  if (!h || variant < FSL_VARIANT_DEFAULT || variant > FSL_VARIANT_PAIR_R80) return FSL_ERR_ARG;
   if ((variant == FSL_VARIANT_QUAD_64 || variant == FSL_VARIANT_PAIR_PIPE) &&
       storage_bytes(h->cfg.precision) != 2)
     return FSL_ERR_ARG;

@@ -85,9 +85,9 @@ struct BulkRing {
   static constexpr int stages = sizeof(typename ST::T) == 2 ? 4 : 3;
   static constexpr size_t pdf_bytes = (size_t)Q * kBulkSeg * sizeof(typename ST::T);
   static constexpr size_t stage_bytes = pdf_bytes + kBulkTX;  // + flag bytes
-  // stages, then full[stages] and empty[stages] barriers, the tile index of
-  // each stage and the abort flag
-  static constexpr size_t bytes = stages * stage_bytes + 2 * stages * 8 + 4 * stages + 16;
+  // stages, then full[stages] and empty[stages] barriers, the tile
+  // coordinates (x0, row, y, z) of each stage and the abort flag
+  static constexpr size_t bytes = stages * stage_bytes + 2 * stages * 8 + 16 * stages + 16;
 };
 
 // List the tiles (TX cells along x of one row) with liquid cells; compact the
@@ -142,8 +142,9 @@ __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
   if (__any_sync(0xffffffffu, liq) && lane == 0) d.l_tiles[atomicAdd(&ctrl->n_tiles, 1u)] = (int)k;
 }
 
-// Update of two neighbouring cells (xa, xa + 1) whose pulled values sit in a
-// staged row segment: stage holds, per direction i, the stored values of
+// Update of two neighbouring cells (xa, xa + 1) of row `row` = (y, z), read
+// from A and written to B, whose pulled values sit in a staged row segment:
+// stage holds, per direction i, the stored values of
 // plane i on the source row (y - c_iy, z - c_iz) from x = x0 - halo on, `seg`
 // values per direction; li is the staged index of cell xa.  Values are read
 // out of shared memory, both cells collide in packed FP32 and the results go
@@ -151,16 +152,16 @@ __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
 // to a wall or obstacle (per-direction path) read HBM instead.  Returns
 // whether a liquid cell reached |u|^2 >= 1/3.
 template <int Q, class ST>
-__device__ __forceinline__ bool bulk_pair(const typename ST::T* stage, int seg, int li, int xa,
-                                          int row, uint8_t fl0, uint8_t fl1, const Dev& d,
-                                          const Geom& g, const Phys& p, const LesLp& les) {
+__device__ __forceinline__ bool bulk_pair(const typename ST::T* __restrict__ A,
+                                          typename ST::T* __restrict__ B,
+                                          const typename ST::T* stage, int seg, int li, int xa,
+                                          int row, int y, int z, uint8_t fl0, uint8_t fl1,
+                                          const Dev& d, const Geom& g, const Phys& p,
+                                          const LesLp& les) {
   using T = typename ST::T;
   constexpr float S = ST::kScaleF;
   const bool liq0 = (fl0 & F_TYPE) == T_LIQ, liq1 = (fl1 & F_TYPE) == T_LIQ;
   if (!liq0 && !liq1) return false;
-  const int cur = d.ctrl->step & 1;
-  const T* __restrict__ A = (const T*)d.pdf[cur];
-  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
   const long long P = g.plane;
   float2 f[Q];
 #pragma unroll
@@ -180,7 +181,6 @@ __device__ __forceinline__ bool bulk_pair(const typename ST::T* stage, int seg, 
       f[i] = make_float2(ST::ld1s(sg + li - cx), ST::ld1s(sg + li + 1 - cx));
     }
   }
-  const int y = row % g.ny, z = row / g.ny;
   if (g.periodic[0] && (xa == 0 || xa + 1 >= g.nx - 1)) {
     // periodic wrap along x: the value comes from the other end of the row
 #pragma unroll
@@ -228,7 +228,7 @@ __device__ __forceinline__ bool bulk_pair(const typename ST::T* stage, int seg, 
 }
 
 template <int Q, class ST>
-__global__ void __launch_bounds__(kBulkThreads, 2)
+__global__ void __launch_bounds__(kBulkThreads, 3)
     k_stream_collide_bulk(Dev d, Geom g, Phys p, int ntx) {
   using T = typename ST::T;
   using RING = BulkRing<Q, ST>;
@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kBulkThreads, 2)
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + D * RING::stage_bytes);
   uint64_t* empty = full + D;
-  int* tile_of = reinterpret_cast<int*>(empty + D);  // tile index held by each stage
+  int4* tile_of = reinterpret_cast<int4*>(empty + D);  // (x0, row, y, z) held by each stage
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tile_of + D);
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
@@ -288,7 +288,8 @@ __global__ void __launch_bounds__(kBulkThreads, 2)
       const unsigned fbytes = (unsigned)(g.sx - x0 < kBulkTX ? g.sx - x0 : kBulkTX);
       unsigned char* stage = smem + (size_t)s * RING::stage_bytes;
       if (lane == 0) {
-        tile_of[s] = k;  // published to the consumers by the arrive below
+        // published to the consumers by the arrive below
+        tile_of[s] = make_int4(x0, row, row % g.ny, row / g.ny);
         mbar_expect_tx(&full[s], bytes * Q + fbytes);
       }
       __syncwarp();
@@ -334,15 +335,13 @@ __global__ void __launch_bounds__(kBulkThreads, 2)
       break;
     }
     const unsigned char* stage = smem + (size_t)s * RING::stage_bytes;
-    const int k = tile_of[s];
-    const int x0 = (k % ntx) * kBulkTX;
-    const int row = k / ntx;
-    const int xa = x0 + 2 * t;
+    const int4 tc = tile_of[s];
+    const int xa = tc.x + 2 * t;
     const uchar2 f2 = *reinterpret_cast<const uchar2*>(stage + RING::pdf_bytes + 2 * t);
     const uint8_t fl0 = xa < g.nx ? f2.x : (uint8_t)T_GAS;
     const uint8_t fl1 = xa + 1 < g.nx ? f2.y : (uint8_t)T_GAS;
-    bad |= bulk_pair<Q, ST>(reinterpret_cast<const T*>(stage), kBulkSeg, kBulkHalo + 2 * t, xa, row,
-                            fl0, fl1, d, g, p, les);
+    bad |= bulk_pair<Q, ST>(A, B, reinterpret_cast<const T*>(stage), kBulkSeg, kBulkHalo + 2 * t,
+                            xa, tc.y, tc.z, tc.w, fl0, fl1, d, g, p, les);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }
@@ -370,8 +369,10 @@ struct WarpRing {
   static constexpr int min_blocks = half ? 3 : 2;  // blocks per SM the ring allows
   static constexpr size_t pdf_bytes = (size_t)Q * kWarpSeg * sizeof(typename ST::T);
   static constexpr size_t stage_bytes = (pdf_bytes + kWarpTX + 15) / 16 * 16;
-  // per warp: stages, then the full barriers and the segment index of each stage
-  static constexpr size_t tail_bytes = (stages * 8 + stages * 4 + 15) / 16 * 16;
+  // per warp: stages, then the full barriers (padded to 16 bytes) and the
+  // segment coordinates (x0, row, y, z) of each stage (16-byte aligned)
+  static constexpr size_t bar_bytes = (stages * 8 + 15) / 16 * 16;
+  static constexpr size_t tail_bytes = bar_bytes + stages * 16;
   static constexpr size_t warp_bytes = stages * stage_bytes + tail_bytes;
   static constexpr size_t bytes = kWarpsPerBlock * warp_bytes;
 };
@@ -391,13 +392,14 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, WarpRing<Q, ST>::min_bloc
   if (gw >= ntl) return;  // whole warp; nothing below synchronises the block
   unsigned char* ring = smem + (size_t)warp * RING::warp_bytes;
   uint64_t* full = reinterpret_cast<uint64_t*>(ring + D * RING::stage_bytes);
-  int* seg_of = reinterpret_cast<int*>(full + D);
+  int4* seg_of = reinterpret_cast<int4*>(ring + D * RING::stage_bytes + RING::bar_bytes);
   if (lane == 0) {
     for (int s = 0; s < D; ++s) mbar_init(&full[s], 1);
     mbar_fence_init();
   }
   __syncwarp();
   const T* __restrict__ A = (const T*)d.pdf[ctrl->step & 1];
+  T* __restrict__ B = (T*)d.pdf[(ctrl->step & 1) ^ 1];
   const long long P = g.plane;
   // copies of the warp's jl-th segment into stage jl % D: lane 0 arms the
   // stage's barrier, then lane i < Q issues direction i and lane Q the flags
@@ -415,7 +417,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, WarpRing<Q, ST>::min_bloc
     const unsigned fbytes = (unsigned)(g.sx - x0 < kWarpTX ? g.sx - x0 : kWarpTX);
     unsigned char* stage = ring + (size_t)s * RING::stage_bytes;
     if (lane == 0) {
-      seg_of[s] = k;  // published to the warp by the arrive below
+      // published to the warp by the arrive below
+      seg_of[s] = make_int4(x0, row, row % g.ny, row / g.ny);
       mbar_expect_tx(&full[s], bytes * Q + fbytes);
     }
     __syncwarp();
@@ -450,15 +453,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, WarpRing<Q, ST>::min_bloc
       break;
     }
     const unsigned char* stage = ring + (size_t)s * RING::stage_bytes;
-    const int k = seg_of[s];
-    const int x0 = (k % ntx) * kWarpTX;
-    const int row = k / ntx;
-    const int xa = x0 + 2 * lane;
+    const int4 tc = seg_of[s];
+    const int xa = tc.x + 2 * lane;
     const uchar2 f2 = *reinterpret_cast<const uchar2*>(stage + RING::pdf_bytes + 2 * lane);
     const uint8_t fl0 = xa < g.nx ? f2.x : (uint8_t)T_GAS;
     const uint8_t fl1 = xa + 1 < g.nx ? f2.y : (uint8_t)T_GAS;
-    bad |= bulk_pair<Q, ST>(reinterpret_cast<const T*>(stage), kWarpSeg, kBulkHalo + 2 * lane, xa,
-                            row, fl0, fl1, d, g, p, les);
+    bad |= bulk_pair<Q, ST>(A, B, reinterpret_cast<const T*>(stage), kWarpSeg,
+                            kBulkHalo + 2 * lane, xa, tc.y, tc.z, tc.w, fl0, fl1, d, g, p, les);
     // this lane's reads of the stage are complete before the refill
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncwarp();

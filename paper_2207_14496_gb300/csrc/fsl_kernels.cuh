@@ -369,15 +369,6 @@ __device__ __forceinline__ V collide_v(const V* f, V* o, float lamE_, float lamO
   const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
   const V uF = vfma(uz, Fz, vfma(uy, Fy, vmul(ux, Fx)));
   const V cst = vfma(vmul(rho, vsplat(-1.5f, z0)), usq, drho);
-  // per weight class (index = |c|^2): constants in storage units
-  V A[4], Bc[4], O[4], GU[4], G9[4], G3[4];
-#pragma unroll
-  for (int c = 0; c < 4; ++c) {
-    const float w = (float)wgt<Q>(c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 7 : (Q == 27 ? 19 : 7));
-    A[c] = vmul(vsplat(4.5f * w * S, z0), rho);
-    Bc[c] = vmul(vsplat(w * S, z0), cst);
-    O[c] = vmul(vsplat(3.0f * w * S, z0), rho);
-  }
   V lamE = vsplat(lamE_, z0), lamO = vsplat(lamO_, z0), pe = vsplat(pe_, z0), po = vsplat(po_, z0);
   if (les.cs > 0.f) {
     // Smagorinsky model (Sec. 2.1) in the pair form: Q_ab = sum_i c_ia c_ib
@@ -387,9 +378,12 @@ __device__ __forceinline__ V collide_v(const V* f, V* o, float lamE_, float lamO
     for (int k = 0; k < NP; ++k) {
       const int i = 2 * k + 1;
       const int c = len2(i);
+      const float wS = (float)wgt<Q>(i) * S;
       const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
       const V cu = vdot(c0, c1, c2, ux, uy, uz);
-      const V dn = vsub(sp[k], vmul(vsplat(2.f, z0), vfma(vmul(A[c], cu), cu, Bc[c])));
+      const V Ac = vmul(vsplat(4.5f * wS, z0), rho), Bcc = vmul(vsplat(wS, z0), cst);
+      const V dn = vsub(sp[k], vmul(vsplat(2.f, z0), vfma(vmul(Ac, cu), cu, Bcc)));
+      (void)c;
       if (c0 != 0) qxx = vadd(qxx, dn);
       if (c1 != 0) qyy = vadd(qyy, dn);
       if (c2 != 0) qzz = vadd(qzz, dn);
@@ -417,16 +411,30 @@ __device__ __forceinline__ V collide_v(const V* f, V* o, float lamE_, float lamO
       Lanes<V>::at(po, l) = __fmaf_rn(-0.5f, lo, 1.f);
     }
   }
+  // The update of a pair (i, i') regrouped: with f_i = (sp + dp)/2,
+  //   f*_i  = a sp + E + (b dp + D),   f*_i' = a sp + E - (b dp + D),
+  //   a = (1 - lam_e)/2, b = (1 - lam_o)/2,
+  //   E = cu (lam_e A cu + pe 9 wS cF) + wS (lam_e cst - 3 pe u.F)   (even part),
+  //   D = lam_o 3 wS rho cu + po 3 wS cF                            (odd part),
+  // A = 4.5 wS rho; wS = w_i S.  Per weight class (index |c|^2):
+  const V r45 = vmul(vmul(lamE, rho), vsplat(4.5f, z0));
+  const V r3 = vmul(vmul(lamO, rho), vsplat(3.0f, z0));
+  const V kb = vfma(lamE, cst, vmul(vmul(vsplat(-3.0f, z0), pe), uF));
+  V Ap[4], Op[4], K[4], G9[4], G3[4];
 #pragma unroll
   for (int c = 0; c < 4; ++c) {
-    const float w = (float)wgt<Q>(c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 7 : (Q == 27 ? 19 : 7));
-    GU[c] = vmul(vmul(vsplat(-3.0f * w * S, z0), pe), uF);
-    G9[c] = vmul(vsplat(9.0f * w * S, z0), pe);
-    G3[c] = vmul(vsplat(3.0f * w * S, z0), po);
+    const float wS = (float)wgt<Q>(c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 7 : (Q == 27 ? 19 : 7)) * S;
+    K[c] = vmul(vsplat(wS, z0), kb);
+    if (c == 0) continue;
+    Ap[c] = vmul(vsplat(wS, z0), r45);
+    Op[c] = vmul(vsplat(wS, z0), r3);
+    G9[c] = vmul(vsplat(9.0f * wS, z0), pe);
+    G3[c] = vmul(vsplat(3.0f * wS, z0), po);
   }
-  // rest population: f0 - [lam_e (f0 - e0) - pe G0]
-  o[0] = vadd(f[0], vfma(lamE, vsub(Bc[0], f[0]), GU[0]));
-  const V m05 = vsplat(-0.5f, z0);
+  const V al = vfma(vsplat(-0.5f, z0), lamE, vsplat(0.5f, z0));
+  const V be = vfma(vsplat(-0.5f, z0), lamO, vsplat(0.5f, z0));
+  // rest population: (1 - lam_e) f0 + wS0 (lam_e cst - 3 pe u.F)
+  o[0] = vfma(vsub(vsplat(1.0f, z0), lamE), f[0], K[0]);
 #pragma unroll
   for (int k = 0; k < NP; ++k) {
     const int i = 2 * k + 1;
@@ -434,16 +442,12 @@ __device__ __forceinline__ V collide_v(const V* f, V* o, float lamE_, float lamO
     const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
     const V cu = vdot(c0, c1, c2, ux, uy, uz);
     const V cF = vdot(c0, c1, c2, Fx, Fy, Fz);
-    const V e = vfma(vmul(A[c], cu), cu, Bc[c]);
-    const V od = vmul(O[c], cu);
-    const V Gp = vfma(vmul(G9[c], cu), cF, GU[c]);
-    const V Gm = vmul(G3[c], cF);
-    // minus the even and odd corrections: lam (e - f+/2... ) + G, each the
-    // exact negation of lam (f+/2 - e) - G
-    const V nDp = vfma(lamE, vfma(m05, sp[k], e), Gp);
-    const V nDm = vfma(lamO, vfma(m05, dp[k], od), Gm);
-    o[i] = vadd(vadd(f[i], nDp), nDm);
-    o[i + 1] = vsub(vadd(f[i + 1], nDp), nDm);
+    const V E = vfma(vfma(Ap[c], cu, vmul(G9[c], cF)), cu, K[c]);
+    const V D = vfma(Op[c], cu, vmul(G3[c], cF));
+    const V Pp = vfma(al, sp[k], E);
+    const V Mm = vfma(be, dp[k], D);
+    o[i] = vadd(Pp, Mm);
+    o[i + 1] = vsub(Pp, Mm);
   }
   return usq;
 }
@@ -1989,7 +1993,7 @@ struct Kernels {
   // resolved bulk-kernel variant of the 16/32-bit path
   static int variant_of(const Geom& g) {
     constexpr bool half = sizeof(typename ST::T) == 2;
-    if ((g.variant >= 1 && g.variant <= 4) || g.variant == 6) return g.variant;
+    if ((g.variant >= 1 && g.variant <= 4) || g.variant == 6 || g.variant == 8) return g.variant;
     if ((g.variant == 5 || g.variant == 7) && half) return g.variant;
     return 2;
   }
@@ -2071,9 +2075,12 @@ struct Kernels {
       } else if (v == 2) {
         dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
         k_stream_collide_lp<Q, ST, 128, 4, false><<<g1, b1, 0, s>>>(d, g, p);
+      } else if (v == 3) {
+        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
+        k_stream_collide_lp<Q, ST, 128, 5, true><<<g1, b1, 0, s>>>(d, g, p);
       } else {
-        dim3 b1(64), g1((g.nx + 127) / 128, g.ny, g.nz);
-        k_stream_collide_lp<Q, ST, 64, 8, false><<<g1, b1, 0, s>>>(d, g, p);
+        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
+        k_stream_collide_lp<Q, ST, 128, 6, true><<<g1, b1, 0, s>>>(d, g, p);
       }
     } else {
       dim3 b1(128), g1((g.nx + 127) / 128, g.ny, g.nz);

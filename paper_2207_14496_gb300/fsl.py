@@ -92,6 +92,16 @@ _lib.fsl_batch_step.argtypes = [_VP, ctypes.c_int]
 _lib.fsl_batch_step.restype = ctypes.c_int
 _lib.fsl_batch_destroy.argtypes = [_VP]
 _lib.fsl_batch_destroy.restype = ctypes.c_int
+_lib.fsl_adjoint_workspace_bytes.argtypes = [_VP, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_SZ)]
+_lib.fsl_adjoint_workspace_bytes.restype = ctypes.c_int
+_lib.fsl_adjoint_create.argtypes = [_VP, ctypes.c_int, ctypes.c_int, _VP, _SZ, ctypes.POINTER(_VP)]
+_lib.fsl_adjoint_create.restype = ctypes.c_int
+_lib.fsl_adjoint_forward.argtypes = [_VP, _VP]
+_lib.fsl_adjoint_forward.restype = ctypes.c_int
+_lib.fsl_adjoint_backward.argtypes = [_VP, _VP, _VP]
+_lib.fsl_adjoint_backward.restype = ctypes.c_int
+_lib.fsl_adjoint_destroy.argtypes = [_VP]
+_lib.fsl_adjoint_destroy.restype = ctypes.c_int
 _lib.fsl_status_string.argtypes = [ctypes.c_int]
 _lib.fsl_status_string.restype = ctypes.c_char_p
 _lib.fsl_last_error.restype = ctypes.c_char_p
@@ -104,9 +114,11 @@ EXPORTED = ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "f
             "fsl_set_trace", "fsl_trace_capacity", "fsl_state_bytes", "fsl_save", "fsl_load",
             "fsl_destroy", "fsl_lattice_table", "fsl_launches_per_step", "fsl_kernel_stats",
             "fsl_status_string", "fsl_last_error", "fsl_total_mass_noalloc", "fsl_set_variant",
-            "fsl_get_variant", "fsl_batch_create", "fsl_batch_step", "fsl_batch_destroy")
-VARIANTS = {"default": 0, "pair": 1, "pair_r128": 2, "pair64_r128": 3, "tma": 4, "quad64": 5, "warp_tma": 6,
-            "pair_pipe": 7}
+            "fsl_get_variant", "fsl_batch_create", "fsl_batch_step", "fsl_batch_destroy",
+            "fsl_adjoint_workspace_bytes", "fsl_adjoint_create", "fsl_adjoint_forward",
+            "fsl_adjoint_backward", "fsl_adjoint_destroy")
+VARIANTS = {"default": 0, "pair": 1, "pair_r128": 2, "pair_r96": 3, "tma": 4, "quad64": 5,
+            "warp_tma": 6, "pair_pipe": 7, "pair_r80": 8}
 KERNEL_STREAM_COLLIDE = 1
 KERNEL_BULK_PASS = 2
 
@@ -356,6 +368,55 @@ class Batch:
         if getattr(self, "b", None) is not None and self.b.value:
             _lib.fsl_batch_destroy(self.b)
             self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Adjoint:
+    """Discrete adjoint of `nsteps` steps of `sim` from its current state,
+    checkpointed every `every` steps (see fsl_adjoint_* in include/fsl.h)."""
+
+    def __init__(self, sim, nsteps: int, every: int = 100):
+        import torch
+
+        self.sim = sim
+        self.nsteps = int(nsteps)
+        n = _SZ()
+        _check(_lib.fsl_adjoint_workspace_bytes(sim.h, self.nsteps, int(every), ctypes.byref(n)),
+               "fsl_adjoint_workspace_bytes")
+        self.bytes = int(n.value)
+        self.workspace = torch.empty(self.bytes + 256, dtype=torch.uint8, device=sim.device)
+        base = (self.workspace.data_ptr() + 255) // 256 * 256
+        a = ctypes.c_void_p()
+        _check(_lib.fsl_adjoint_create(sim.h, self.nsteps, int(every), ctypes.c_void_p(base),
+                                       self.bytes, ctypes.byref(a)), "fsl_adjoint_create")
+        self.a = a
+
+    def forward(self) -> np.ndarray:
+        """Run the steps; the column height after each step."""
+        col = np.zeros(self.nsteps)
+        _check(_lib.fsl_adjoint_forward(self.a, _ptr(col)), "fsl_adjoint_forward")
+        return col
+
+    def backward(self, dj_dcolumn) -> dict:
+        dj = np.ascontiguousarray(np.asarray(dj_dcolumn, dtype=np.float64))
+        assert dj.size == self.nsteps
+        nx, ny, nz = self.sim.shape
+        out = np.zeros(4 + 2 * self.sim.N)
+        _check(_lib.fsl_adjoint_backward(self.a, _ptr(dj), _ptr(out)), "fsl_adjoint_backward")
+        n = self.sim.N
+        return dict(nu=float(out[0]), g=out[1:4].copy(),
+                    drho0=out[4:4 + n].reshape(nz, ny, nx),
+                    dphi0=out[4 + n:4 + 2 * n].reshape(nz, ny, nx))
+
+    def close(self):
+        if getattr(self, "a", None) is not None and self.a.value:
+            _lib.fsl_adjoint_destroy(self.a)
+            self.a = None
 
     def __del__(self):
         try:

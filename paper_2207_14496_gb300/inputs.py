@@ -48,6 +48,23 @@ def wave_fill(nx: int, ny: int, nz: int, depth: float, amp: float, wavelength: f
     return np.ascontiguousarray(np.broadcast_to(phi2, (nz, ny, nx)))
 
 
+def wave_fill_dperturb(nx: int, ny: int, depth: float, amp: float, wavelength: float,
+                       perturb=None) -> np.ndarray:
+    """d phi(i, j) / d perturb[i] of wave_fill, shape (ny, nx): the fraction of
+    the cell's width (same quadrature) where 0 < h(x) - j < 1."""
+    xg, wg = np.polynomial.legendre.leggauss(64)
+    k = 2.0 * math.pi / wavelength
+    i = np.arange(nx, dtype=np.float64)
+    xs = i[:, None] + 0.5 * xg[None, :]
+    h = depth + amp * np.cos(k * xs)
+    if perturb is not None:
+        h = h + np.asarray(perturb, dtype=np.float64)[:, None]
+    j = np.arange(ny, dtype=np.float64)
+    r = h[None, :, :] - j[:, None, None]
+    inside = ((r > 0.0) & (r < 1.0)).astype(np.float64)
+    return 0.5 * np.tensordot(inside, wg, axes=([2], [0]))
+
+
 def box_fill(nx: int, ny: int, nz: int, width: int, height: int) -> np.ndarray:
     """Liquid column occupying cells i < width, j < height (all k)."""
     phi = np.zeros((nz, ny, nx))

@@ -9,7 +9,7 @@ from paper_2207_14496_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-VARIANTS = ["pair", "pair_r128", "pair64_r128", "tma", "quad64", "warp_tma", "pair_pipe"]
+VARIANTS = ["pair", "pair_r128", "pair_r96", "pair_r80", "tma", "quad64", "warp_tma", "pair_pipe"]
 HALF_ONLY = ("quad64", "pair_pipe")
 
 
