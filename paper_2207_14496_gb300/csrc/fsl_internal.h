@@ -42,6 +42,10 @@ struct Ctrl {
 
 constexpr int kTraceCapacity = 1 << 16;
 constexpr int kListBlocks = 2 * 152;  // grid of the list-driven kernels
+// grid of the two kernels that run one thread per interface cell (tens of
+// thousands per step): enough threads for one cell each, so that their
+// latency-bound neighbourhood reads overlap across many warps
+constexpr int kCellListBlocks = 8 * 152;
 constexpr int kReduceBlocks = 4 * 152;
 
 struct Geom {

@@ -1952,14 +1952,14 @@ struct Kernels {
     cudaError_t e = pre_bulk(d, g, p, s);
     if (e == cudaSuccess) e = stream_collide(d, g, p, s);
     if (e != cudaSuccess) return e;
-    k_stream_collide_if<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
+    k_stream_collide_if<Q, ST><<<kCellListBlocks, 128, 0, s>>>(d, g, p);
     k_fill<Q><<<kListBlocks, 256, 0, s>>>(d, g);
     k_empty<Q, ST><<<kListBlocks, 256, 0, s>>>(d, g);
     k_finalise<<<kListBlocks, 256, 0, s>>>(d);
     k_refill<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
     k_excess_share<Q><<<kListBlocks, 256, 0, s>>>(d, g);
     k_excess_gather<Q><<<kListBlocks, 256, 0, s>>>(d, g);
-    k_classify<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
+    k_classify<Q, ST><<<kCellListBlocks, 128, 0, s>>>(d, g, p);
     k_end_step<<<kEndBlocks, 256, 0, s>>>(d, g);
     return cudaGetLastError();
   }
