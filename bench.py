@@ -302,7 +302,7 @@ def main():
                         peak_source="152 SMs x 2 FP64 lanes/clk x 2.07 GHz, one op per instruction")
         ach = r["kernel_bytes"] / (r["kernel_ms"] * 1e-3) / 1e9
         return dict(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
-                    frac=ach / peaks["hbm_gbs"], traffic=TRAFFIC.get(prec),
+                    frac=ach / peaks["hbm_gbs"], traffic=TRAFFIC.get((prec, r["variant"])),
                     kernel=KERNEL_OF.get(r["variant"], "k_stream_collide_lp"),
                     variant=r["variant"], peak_source=peaks["source"])
 
@@ -356,7 +356,11 @@ def main():
 FLOPS_PER_CELL_D3Q27_TRT = 1060
 # DRAM bytes per launch of k_stream_collide from the ncu capture summarised
 # under profiles/ (null until captured for the current kernel).
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the bulk kernel at 256^3, from one
+# ncu capture per (storage, variant) on the 160^3 case scaled by the
+# launches' algorithmic bytes; None for a
+# kernel without a capture of its current code.
+TRAFFIC = {("fp16", "pair_r96"): 562e6}
 
 if __name__ == "__main__":
     main()
