@@ -103,7 +103,11 @@ fsl_status fsl_workspace_bytes(const fsl_config* cfg, size_t* bytes);
 /* Bind a configuration to a caller-owned device workspace and CUDA stream
  * (cudaStream_t passed as void*; NULL = legacy default stream).
  * d_workspace: device pointer, 256-byte aligned, >= fsl_workspace_bytes.
- * out: receives the host handle (release with fsl_destroy). */
+ * out: receives the host handle (release with fsl_destroy).  The handle
+ * creates one high-priority side stream and two events of its own (no device
+ * memory): each step runs its interface-cell pass there, forked from and
+ * joined back to the bound stream, beside the bulk pass; fsl_destroy
+ * releases them. */
 fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, void* cuda_stream,
                       fsl_handle** out);
 
@@ -210,8 +214,8 @@ int fsl_get_variant(const fsl_handle* h);
  * events, and leaves the simulation state unchanged (the pass only reads the
  * current PDF buffer and writes the other one).  out4 (host, 4 doubles):
  * average launch time in ms, algorithmic bytes per launch (liquid cells x
- * 2 q x storage bytes + one flag byte per cell + 4 bytes per interface cell
- * listed), number of liquid cells, number of interface cells.  Synchronises
+ * 2 q x storage bytes + one flag byte per cell), number of liquid cells,
+ * number of interface cells.  Synchronises
  * the stream.  FSL_ERR_ARG for another kernel code or reps < 1. */
 enum { FSL_KERNEL_STREAM_COLLIDE = 1, FSL_KERNEL_BULK_PASS = 2 };
 fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4);

@@ -36,7 +36,7 @@ constexpr long long kPlaneSkew = 512;  // elements added to every PDF plane
 
 enum Region {
   R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST,
-  R_LIF, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_LTILES, R_CTRL, R_TRACE, R_RED, R_COUNT
+  R_LIF, R_LIF2, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_LTILES, R_CTRL, R_TRACE, R_RED, R_COUNT
 };
 
 bool valid_config(const fsl_config* c) {
@@ -244,6 +244,7 @@ struct fsl_handle {
   std::map<int, cudaGraphExec_t> graphs;
   unsigned gen = 0;  // bumped whenever captured launch parameters may change
   char* base = nullptr;         // start of the workspace
+  Aux aux = {nullptr, nullptr, nullptr};  // side stream of the interface pass
   double h_ref = 0.0;           // hydrostatic reference height of the last fsl_init_fill
 };
 
@@ -312,6 +313,7 @@ fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, vo
   d.mex = reinterpret_cast<double*>(base + h->off[R_MEX]);
   d.lost = reinterpret_cast<double*>(base + h->off[R_LOST]);
   d.l_if = reinterpret_cast<int*>(base + h->off[R_LIF]);
+  d.l_if2 = reinterpret_cast<int*>(base + h->off[R_LIF2]);
   d.l_fill = reinterpret_cast<int*>(base + h->off[R_LFILL]);
   d.l_empty = reinterpret_cast<int*>(base + h->off[R_LEMPTY]);
   d.l_new = reinterpret_cast<int*>(base + h->off[R_LNEW]);
@@ -324,6 +326,23 @@ fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, vo
   d.redi = nullptr;
   h->L = L;
   h->stream = static_cast<cudaStream_t>(cuda_stream);
+  {
+    // the interface pass runs on a high-priority side stream beside the bulk
+    // pass; if it cannot be created the step uses one stream
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    Aux a = {nullptr, nullptr, nullptr};
+    if (cudaStreamCreateWithPriority(&a.side, cudaStreamNonBlocking, hi) == cudaSuccess &&
+        cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&a.join, cudaEventDisableTiming) == cudaSuccess) {
+      h->aux = a;
+    } else {
+      if (a.join) cudaEventDestroy(a.join);
+      if (a.fork) cudaEventDestroy(a.fork);
+      if (a.side) cudaStreamDestroy(a.side);
+      cudaGetLastError();
+    }
+  }
   h->ready = false;
   h->trace_every = 0;
   *out = h;
@@ -370,7 +389,7 @@ fsl_status fsl_step(fsl_handle* h, int nsteps) {
   if (h->stream) FSL_CK(cudaStreamIsCapturing(h->stream, &cs));
   if (!h->stream || cs != cudaStreamCaptureStatusNone) {
     // legacy default stream (not capturable) or a capture owned by the caller
-    for (int k = 0; k < nsteps; ++k) FSL_CK(h->L->step(h->d, h->g, h->p, h->stream));
+    for (int k = 0; k < nsteps; ++k) FSL_CK(h->L->step(h->d, h->g, h->p, h->stream, h->aux));
     return FSL_OK;
   }
   int left = nsteps;
@@ -381,7 +400,7 @@ fsl_status fsl_step(fsl_handle* h, int nsteps) {
       cudaGraph_t graph;
       FSL_CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t le = cudaSuccess;
-      for (int k = 0; k < chunk && le == cudaSuccess; ++k) le = h->L->step(h->d, h->g, h->p, h->stream);
+      for (int k = 0; k < chunk && le == cudaSuccess; ++k) le = h->L->step(h->d, h->g, h->p, h->stream, h->aux);
       cudaError_t ee = cudaStreamEndCapture(h->stream, &graph);
       if (le != cudaSuccess) return cuda_fail(le, "step launch during capture");
       if (ee != cudaSuccess) return cuda_fail(ee, "cudaStreamEndCapture");
@@ -593,8 +612,12 @@ fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
   c.n_emptied = c.end_blocks = c.n_tiles = 0;
   c.trace_every = h->trace_every;
   c.trace_count = 0;
+  c.n_if_next = 0;
   FSL_CK(cudaMemcpyAsync(h->d.ctrl, &c, sizeof(Ctrl), cudaMemcpyHostToDevice, h->stream));
   FSL_CK(cudaMemsetAsync(h->d.claim, 0, (size_t)h->g.cells, h->stream));
+  // the interface list of the loaded step, from the loaded flags
+  k_list_interface<<<4 * 152, 256, 0, h->stream>>>(h->d, h->g);
+  FSL_CK(cudaGetLastError());
   FSL_CK(cudaStreamSynchronize(h->stream));
   h->ready = true;
   return FSL_OK;
@@ -603,6 +626,12 @@ fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
 fsl_status fsl_destroy(fsl_handle* h) {
   if (!h) return FSL_ERR_ARG;
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  if (h->aux.side) {
+    cudaStreamSynchronize(h->aux.side);
+    cudaEventDestroy(h->aux.fork);
+    cudaEventDestroy(h->aux.join);
+    cudaStreamDestroy(h->aux.side);
+  }
   delete h;
   return FSL_OK;
 }
@@ -919,7 +948,7 @@ fsl_status batch_capture(fsl_batch* b, int steps, cudaGraphExec_t* out) {
       return cuda_fail(e, "cudaStreamBeginCapture (batch)");
     }
     cudaError_t le = cudaSuccess;
-    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = h->L->step(h->d, h->g, h->p, b->cap);
+    for (int k = 0; k < steps && le == cudaSuccess; ++k) le = h->L->step(h->d, h->g, h->p, b->cap, h->aux);
     e = cudaStreamEndCapture(b->cap, &g);
     if (le != cudaSuccess || e != cudaSuccess) {
       if (e == cudaSuccess) cudaGraphDestroy(g);
@@ -1063,10 +1092,8 @@ fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
     if (err == cudaSuccess) err = h->L->pre_bulk(h->d, h->g, h->p, h->stream);
   }
   for (int r = 0; r < reps && err == cudaSuccess; ++r) {
-    // the lists are rebuilt by whichever kernel builds them in a step
-    if (with_pre || h->L->launches_per_step(h->g) == 11)
-      err = cudaMemsetAsync(&h->d.ctrl->n_if, 0, sizeof(unsigned), h->stream);
-    if (err == cudaSuccess && with_pre)
+    // the tile list is rebuilt by the pre-pass
+    if (with_pre)
       err = cudaMemsetAsync(&h->d.ctrl->n_tiles, 0, sizeof(unsigned), h->stream);
     if (err == cudaSuccess) err = cudaEventRecord(e0, h->stream);
     if (err == cudaSuccess && with_pre) err = h->L->pre_bulk(h->d, h->g, h->p, h->stream);
@@ -1077,7 +1104,6 @@ fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
     if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
     total_ms += ms;
   }
-  if (err == cudaSuccess) err = cudaMemsetAsync(&h->d.ctrl->n_if, 0, sizeof(unsigned), h->stream);
   if (err == cudaSuccess) err = cudaMemsetAsync(&h->d.ctrl->n_tiles, 0, sizeof(unsigned), h->stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize(h->stream);
   cudaEventDestroy(e0);
@@ -1086,9 +1112,8 @@ fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
   const double sb = (double)storage_bytes(h->cfg.precision);
   const double cells = (double)h->g.nx * h->g.ny * h->g.nz;
   out4[0] = total_ms / reps;
-  // liquid cells read and write q PDFs; every cell's flag byte is read; each
-  // interface cell index is appended to the interface list
-  out4[1] = (double)nc[0] * 2.0 * h->cfg.lattice * sb + cells * 1.0 + (double)nc[1] * 4.0;
+  // liquid cells read and write q PDFs; every cell's flag byte is read
+  out4[1] = (double)nc[0] * 2.0 * h->cfg.lattice * sb + cells * 1.0;
   out4[2] = (double)nc[0];
   out4[3] = (double)nc[1];
   return FSL_OK;

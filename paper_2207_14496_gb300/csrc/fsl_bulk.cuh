@@ -1,8 +1,7 @@
 // Bulk pass of the 16/32-bit path, staged through shared memory by the TMA.
 //
 // k_tiles lists, at the start of a step, the tiles (256 cells along x of one
-// (y, z) row) that hold liquid cells, and compacts the interface cells of
-// every tile into the interface list (warp ballots).
+// (y, z) row) that hold liquid cells.
 //
 // k_stream_collide_bulk is persistent and warp-specialised.  Its producer warp
 // walks the CTA's share of the tile list and, for each tile, issues Q + 1
@@ -90,8 +89,8 @@ struct BulkRing {
   static constexpr size_t bytes = stages * stage_bytes + 2 * stages * 8 + 16 * stages + 16;
 };
 
-// List the tiles (TX cells along x of one row) with liquid cells; compact the
-// interface cells.  One warp per tile, TX / 32 consecutive cells per lane.
+// List the tiles (TX cells along x of one row) with liquid cells.  One warp
+// per tile, TX / 32 consecutive cells per lane.
 template <int TX>
 __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
   constexpr int CPL = TX / 32;
@@ -115,29 +114,11 @@ __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
     }
   }
   bool liq = false;
-  unsigned m[CPL];
-  unsigned total = 0;
 #pragma unroll
   for (int b = 0; b < CPL; ++b) {
     const unsigned byte = ((b < 4 ? f8.x : f8.y) >> (8 * (b & 3))) & 0xffu;
     const bool in = xl + b < g.nx;
-    const int t = in ? (int)(byte & F_TYPE) : T_GAS;
-    liq |= t == T_LIQ;
-    m[b] = __ballot_sync(0xffffffffu, t == T_IF);
-    total += __popc(m[b]);
-  }
-  // one list reservation per warp for its interface cells
-  if (total) {
-    unsigned base = 0;
-    if (lane == 0) base = atomicAdd(&ctrl->n_if, total);
-    base = __shfl_sync(0xffffffffu, base, 0);
-    const unsigned below = (1u << lane) - 1u;
-    // list order: cell by cell within the lane's run, lanes in order
-#pragma unroll
-    for (int b = 0; b < CPL; ++b) {
-      if ((m[b] >> lane) & 1u) d.l_if[base + __popc(m[b] & below)] = (int)(row * g.sx + xl + b);
-      base += __popc(m[b]);
-    }
+    liq |= in && (int)(byte & F_TYPE) == T_LIQ;
   }
   if (__any_sync(0xffffffffu, liq) && lane == 0) d.l_tiles[atomicAdd(&ctrl->n_tiles, 1u)] = (int)k;
 }

@@ -25,7 +25,7 @@ enum : uint8_t {
 struct Ctrl {
   int step;            // steps completed
   int unstable_step;   // first step with |u| >= c_s or NaN, -1 if none
-  unsigned n_if;       // interface cells seen by the stream-collide pass
+  unsigned n_if;       // interface cells of this step (list built by the previous step)
   unsigned n_fill;     // cells marked to fill
   unsigned n_empty;    // cells marked to empty
   unsigned n_new;      // gas -> interface cells
@@ -38,6 +38,7 @@ struct Ctrl {
   unsigned n_emptied;  // to-gas cells actually converted this step
   unsigned end_blocks; // end-of-step blocks finished
   unsigned n_tiles;    // tiles holding liquid cells, listed this step (16/32-bit path)
+  unsigned n_if_next;  // interface cells of the next step (appended by k_classify)
 };
 
 constexpr int kTraceCapacity = 1 << 16;
@@ -93,7 +94,8 @@ struct Dev {
   double* kappa;      // curvature K (interface cells)
   double* mex;        // excess mass of converted cells / share per receiver
   double* lost;       // per-cell lost excess mass (no receiver)
-  int* l_if;
+  int* l_if;   // interface list of even steps
+  int* l_if2;  // interface list of odd steps
   int* l_fill;
   int* l_empty;
   int* l_new;
@@ -107,9 +109,17 @@ struct Dev {
 };
 
 // Per-precision-family launch table, implemented in fsl_prec_*.cu.
+// Side stream and events of a handle: the interface pass of a step runs on
+// `side`, forked from and joined back to the step's stream, concurrently with
+// the bulk pass (the two write disjoint cells).  side == nullptr: one stream.
+struct Aux {
+  cudaStream_t side;
+  cudaEvent_t fork, join;
+};
+
 struct Launch {
   // one full time step from pdf[step & 1] to pdf[(step + 1) & 1]
-  cudaError_t (*step)(const Dev&, const Geom&, const Phys&, cudaStream_t);
+  cudaError_t (*step)(const Dev&, const Geom&, const Phys&, cudaStream_t, const Aux&);
   // initial state into pdf[cur] (cur = 0); staged: fill level in d.phinew and
   // obstacle bytes in d.claim (both unpadded), u0 (3N doubles, unpadded) in
   // stage_u or null

@@ -5,15 +5,18 @@
 // FP64 evaluation in the operation order written here.
 //
 // One step (Sec. 2 and 3 of the paper), t -> t+1:
-//   k_stream_collide  pull streaming (Eq. nm-lbm-streaming), halfway bounce-back,
-//                     free-surface anti-bounce-back for PDFs from gas
+//   k_stream_collide  (bulk variants) pull streaming (Eq. nm-lbm-streaming),
+//                     halfway bounce-back, moments (Eqs. nm-lbm-density,
+//                     nm-lbm-velocity), SRT/TRT collision with Guo forcing
+//                     (Eqs. nm-lbm-collision, nm-lbm-force-guo) of the liquid
+//                     cells; concurrently, on a second stream,
+//   k_stream_collide_if  the interface cells of the list built by the previous
+//                     step: free-surface anti-bounce-back for PDFs from gas
 //                     (Eq. nm-fslbm-boundary-condition), interface mass flux
-//                     (Eq. nm-fslbm-mass-flux, Thuerey classes), moments
-//                     (Eqs. nm-lbm-density, nm-lbm-velocity), SRT/TRT collision
-//                     with Guo forcing (Eqs. nm-lbm-collision, nm-lbm-force-guo),
+//                     (Eq. nm-fslbm-mass-flux, Thuerey classes), collision,
 //                     fill level m/rho (Eq. nm-fslbm-mass), conversion marks
 //                     (threshold eps_phi) and warp-ballot compaction of the
-//                     interface, to-liquid and to-gas cells;
+//                     to-liquid and to-gas cells;
 //   k_fill            commit fill levels; gas neighbours of filled cells become
 //                     new interface cells; to-gas neighbours are kept (filling
 //                     wins a conflict);
@@ -23,7 +26,8 @@
 //   k_excess_share    share per receiver, receiver compaction;
 //   k_excess_gather   receivers gather their shares in direction order;
 //   k_classify        Thuerey classes and curvature K = -div(n_hat) for the
-//                     next step, clean-up of the per-step marks;
+//                     next step, clean-up of the per-step marks, and the next
+//                     step's interface list (two lists, by step parity);
 //   k_end_step        trace record, counters, step counter.
 #pragma once
 #include "fsl_lattice.cuh"
@@ -489,8 +493,6 @@ __global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, P
     fl1 = x0 + 1 < g.nx ? fl.y : (uint8_t)T_GAS;
   }
   const int t0 = fl0 & F_TYPE, t1 = fl1 & F_TYPE;
-  warp_append(t0 == T_IF, row + x0, &ctrl->n_if, d.l_if);
-  warp_append(t1 == T_IF, row + x0 + 1, &ctrl->n_if, d.l_if);
   const bool liq0 = t0 == T_LIQ, liq1 = t1 == T_LIQ;
   if (!__any_sync(FULL, liq0 || liq1)) return;
   // rows of the y/z neighbours (a wall side maps to the cell's own row: such
@@ -617,7 +619,6 @@ __global__ void __launch_bounds__(64) k_stream_collide_lp4(Dev d, Geom g, Phys p
   bool anyl = false;
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    warp_append((fl[k] & F_TYPE) == T_IF, row + x0 + k, &ctrl->n_if, d.l_if);
     anyl |= (fl[k] & F_TYPE) == T_LIQ;
   }
   if (!__any_sync(FULL, anyl)) return;
@@ -795,8 +796,6 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pp(Dev d, Geom g, Phy
     // row r: interface cells to the list, liquid cells stream and collide
     const long long row = (long long)r * g.sx;
     const uint8_t fl0 = (uint8_t)(fc & 0xffu), fl1 = (uint8_t)(fc >> 8);
-    warp_append((fl0 & F_TYPE) == T_IF, (int)(row + x0), &ctrl->n_if, d.l_if);
-    warp_append((fl1 & F_TYPE) == T_IF, (int)(row + x0 + 1), &ctrl->n_if, d.l_if);
     if (anyc) {
       const bool liq0 = (fl0 & F_TYPE) == T_LIQ, liq1 = (fl1 & F_TYPE) == T_LIQ;
       float2 f[Q];
@@ -876,8 +875,8 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pp(Dev d, Geom g, Phy
 namespace fsl {
 
 // ------------------------------------------------------------ stream-collide
-// Pass over all cells: liquid cells stream and collide here; interface cells
-// are compacted (warp ballot) into l_if for k_stream_collide_if.
+// Pass over all cells: liquid cells stream and collide here (interface cells
+// are handled by k_stream_collide_if from the step's interface list).
 template <int Q, class ST>
 __global__ void __launch_bounds__(128) k_stream_collide(Dev d, Geom g, Phys p) {
   using T = typename ST::T;
@@ -904,7 +903,6 @@ __global__ void __launch_bounds__(128) k_stream_collide(Dev d, Geom g, Phys p) {
 #pragma unroll
     for (int i = 0; i < Q; ++i) ST::stw(B + i * P + c, fout[i]);
   }
-  warp_append(type == T_IF, c, &ctrl->n_if, d.l_if);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
     atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
 }
@@ -923,10 +921,11 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
   T* __restrict__ B = (T*)d.pdf[cur ^ 1];
   const long long P = g.plane;
   const unsigned nif = ctrl->n_if;
+  const int* lif = list_if(d, ctrl->step);
   bool bad = false;
   FSL_WARP_LOOP(k, ok, nif) {
     bool to_liq = false, to_gas = false;
-    const int c = ok ? d.l_if[k] : 0;
+    const int c = ok ? lif[k] : 0;
     if (ok) {
     int x, y, z;
     cell_xyz(g, c, x, y, z);
@@ -1035,9 +1034,10 @@ __global__ void __launch_bounds__(256) k_fill(Dev d, Geom g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nif = ctrl->n_if, nfill = ctrl->n_fill;
+  const int* lif = list_if(d, ctrl->step);
   // commit the fill levels computed by the stream-collide pass
   FSL_GRID_LOOP(k, nif) {
-    const int c = d.l_if[k];
+    const int c = lif[k];
     d.phi[c] = d.phinew[c];
   }
   // gas neighbours of filled cells become new interface cells; a neighbour
@@ -1620,18 +1620,42 @@ __global__ void __launch_bounds__(128) k_classify(Dev d, Geom g, Phys p) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned a = ctrl->n_if, b = ctrl->n_new, e = ctrl->n_l2i;
-  FSL_GRID_LOOP(k, a + b + e) {
-    const int c = k < a ? d.l_if[k] : (k < a + b ? d.l_new[k - a] : d.l_l2i[k - a - b]);
-    const uint8_t fl = d.flags[c];
-    uint8_t nf = (uint8_t)(fl & ~(F_TO_LIQ | F_TO_GAS | F_NEW | F_NF | F_NE));
-    d.claim[c] = 0;
-    if ((fl & F_TYPE) == T_IF) {
-      int x, y, z;
-      cell_xyz(g, c, x, y, z);
-      nf |= iface_class<Q>(g, d.flags, x, y, z);
-      d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, d.phi, x, y, z) : 0.0;
+  const int* lif = list_if(d, ctrl->step);
+  int* lnext = list_if(d, ctrl->step + 1);
+  // every interface cell of the next step was interface, new or liquid turned
+  // interface in this one: the next step's list is built here
+  FSL_WARP_LOOP(k, ok, a + b + e) {
+    const int c = !ok ? 0 : (k < a ? lif[k] : (k < a + b ? d.l_new[k - a] : d.l_l2i[k - a - b]));
+    bool is_if = false;
+    if (ok) {
+      const uint8_t fl = d.flags[c];
+      uint8_t nf = (uint8_t)(fl & ~(F_TO_LIQ | F_TO_GAS | F_NEW | F_NF | F_NE));
+      d.claim[c] = 0;
+      if ((fl & F_TYPE) == T_IF) {
+        is_if = true;
+        int x, y, z;
+        cell_xyz(g, c, x, y, z);
+        nf |= iface_class<Q>(g, d.flags, x, y, z);
+        d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, d.phi, x, y, z) : 0.0;
+      }
+      d.flags[c] = nf;
     }
-    d.flags[c] = nf;
+    warp_append(is_if, c, &ctrl->n_if_next, lnext);
+  }
+}
+
+// The interface list of the current step from the flags (initial state, state
+// loaded from a checkpoint).
+static __global__ void k_list_interface(Dev d, Geom g) {
+  Ctrl* ctrl = d.ctrl;
+  int* lif = list_if(d, ctrl->step);
+  FSL_WARP_LOOP(k, ok, (unsigned)g.cells) {
+    bool is_if = false;
+    if (ok) {
+      const int x = (int)(k % (unsigned)g.sx);
+      is_if = x < g.nx && (d.flags[k] & F_TYPE) == T_IF;
+    }
+    warp_append(is_if, (int)k, &ctrl->n_if, lif);
   }
 }
 
@@ -1739,7 +1763,9 @@ static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
     ctrl->last[1] = ctrl->n_emptied;
     ctrl->last[2] = ctrl->n_new;
     ctrl->last[3] = ctrl->n_if;
-    ctrl->n_if = ctrl->n_fill = ctrl->n_empty = 0;
+    ctrl->n_if = ctrl->n_if_next;  // the list k_classify built for the next step
+    ctrl->n_if_next = 0;
+    ctrl->n_fill = ctrl->n_empty = 0;
     ctrl->n_new = ctrl->n_l2i = ctrl->n_recv = 0;
     ctrl->n_emptied = 0;
     ctrl->end_blocks = 0;
@@ -1948,11 +1974,26 @@ template <int Q, class ST>
 struct Kernels {
   // the buffer parity is read on the device from the step counter, so the
   // launch sequence is the same for every step (and graph-capturable)
-  static cudaError_t step(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
-    cudaError_t e = pre_bulk(d, g, p, s);
+  static cudaError_t step(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s,
+                          const Aux& aux) {
+    // the interface pass (its list was built by the previous step) beside the
+    // bulk pass: disjoint cells written, same input buffer read
+    cudaStream_t si = aux.side ? aux.side : s;
+    cudaError_t e = cudaSuccess;
+    if (aux.side) {
+      e = cudaEventRecord(aux.fork, s);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(aux.side, aux.fork, 0);
+      if (e != cudaSuccess) return e;
+    }
+    k_stream_collide_if<Q, ST><<<kCellListBlocks, 128, 0, si>>>(d, g, p);
+    if (aux.side) {
+      e = cudaEventRecord(aux.join, aux.side);
+      if (e != cudaSuccess) return e;
+    }
+    e = pre_bulk(d, g, p, s);
     if (e == cudaSuccess) e = stream_collide(d, g, p, s);
+    if (e == cudaSuccess && aux.side) e = cudaStreamWaitEvent(s, aux.join, 0);
     if (e != cudaSuccess) return e;
-    k_stream_collide_if<Q, ST><<<kCellListBlocks, 128, 0, s>>>(d, g, p);
     k_fill<Q><<<kListBlocks, 256, 0, s>>>(d, g);
     k_empty<Q, ST><<<kListBlocks, 256, 0, s>>>(d, g);
     k_finalise<<<kListBlocks, 256, 0, s>>>(d);
@@ -1971,6 +2012,7 @@ struct Kernels {
     k_init_close<Q><<<blocks, 256, 0, s>>>(d, g);
     k_init_state<Q, ST><<<blocks, 256, 0, s>>>(d, g, p, cur, u0, h_ref);
     k_init_classes<Q, ST><<<blocks, 128, 0, s>>>(d, g, p);
+    k_list_interface<<<blocks, 256, 0, s>>>(d, g);
     return cudaGetLastError();
   }
   static cudaError_t total_mass(const Dev& d, const Geom& g, const Phys&, int cur, double* out,

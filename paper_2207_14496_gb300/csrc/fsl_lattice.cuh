@@ -231,6 +231,9 @@ __device__ __forceinline__ int type_at(const uint8_t* flags, int c) {
 }
 __device__ __forceinline__ bool is_fluid(int t) { return t == T_LIQ || t == T_IF; }
 
+// the interface list consumed in step `step` (built by step - 1)
+__device__ __forceinline__ int* list_if(const Dev& d, int step) { return (step & 1) ? d.l_if2 : d.l_if; }
+
 // frozen: an instability was latched in an earlier step
 __device__ __forceinline__ bool frozen(const Ctrl* ctrl) {
   int u = *(volatile const int*)&ctrl->unstable_step;
