@@ -360,7 +360,7 @@ FLOPS_PER_CELL_D3Q27_TRT = 1060
 # ncu capture per (storage, variant) on the 160^3 case scaled by the
 # launches' algorithmic bytes; None for a
 # kernel without a capture of its current code.
-TRAFFIC = {("fp16", "pair_r96"): 562e6}
+TRAFFIC = {("fp16", "pair_r96"): 568e6}
 
 if __name__ == "__main__":
     main()
