@@ -106,6 +106,24 @@ class ClockSampler:
                     sm_max_mhz=max(smax) if smax else None, reasons=reasons, samples=len(rows))
 
 
+def reduce_max(v: float, world: int, device: str) -> float:
+    """Maximum of a per-rank value over the ranks of the default process
+    group (the slowest replica sets the job's time)."""
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_mlups(cells: int, steps: int, ms_max: float, world: int) -> float:
+    """Whole-job throughput of `world` independent replicas of a domain of
+    `cells` cells, each advanced `steps` steps, the slowest in ms_max ms."""
+    return world * cells * steps / (ms_max * 1e-3) / 1e6
+
+
 def time_precision(fsl, w, precision, steps, warmup, dev, barrier):
     """Device-resident timing: CUDA events on the library's stream around K
     steps (captured CUDA graphs), after W warm-up steps."""
@@ -259,11 +277,7 @@ def main():
             dist.barrier()
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_max(v, world, f"cuda:{local}")
 
     from paper_2207_14496_gb300 import build, inputs
     build.build()
@@ -288,7 +302,7 @@ def main():
     h = res[head]
     ms_max = max_over_ranks(h["ms"])
     n_cells = int(np.prod(w["params"]["shape"]))
-    value = world * n_cells * h["steps"] / (ms_max * 1e-3) / 1e6
+    value = replica_mlups(n_cells, h["steps"], ms_max, world)
 
     def roofline(r, prec):
         if prec == "fp64":
