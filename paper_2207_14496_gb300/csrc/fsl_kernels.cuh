@@ -997,7 +997,19 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
     }
     const double m_new = dm_has ? d.mass[c] + (double)dm : d.mass[c];
     R fout[Q], rho;
-    const R usq = collide<Q, SH, R>(fin, fout, p, rho);
+    R usq;
+    if constexpr (SH) {
+      // 16/32-bit path: the regrouped pair collision of the bulk kernels, on
+      // unscaled offsets (scale 1); rho summed in the same pair order
+      R drho;
+      density<Q, SH, R>(fin, rho, drho);
+      const bool tr = p.trt != 0;
+      usq = collide_v<Q, float>(fin, fout, p.f.lam_e, tr ? p.f.lam_o : p.f.omega, p.f.pre_e,
+                                tr ? p.f.pre_o : p.f.pre_e, p.f.g[0], p.f.g[1], p.f.g[2], 1.0f,
+                                LesLp::of(p));
+    } else {
+      usq = collide<Q, SH, R>(fin, fout, p, rho);
+    }
     if (!(usq < (R)(1.0 / 3.0))) bad = true;
 #pragma unroll
     for (int i = 0; i < Q; ++i) ST::stw(B + i * P + c, fout[i]);
