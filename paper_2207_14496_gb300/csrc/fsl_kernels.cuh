@@ -831,18 +831,9 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pp(Dev d, Geom g, Phy
           }
         }
       }
-      float2 usq = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!(h ? liq1 : liq0)) continue;
-        float c[Q];
-#pragma unroll
-        for (int i = 0; i < Q; ++i) c[i] = Lanes<float2>::at(f[i], h);
-        Lanes<float2>::at(usq, h) =
-            collide_v<Q, float>(c, c, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2], S, les);
-#pragma unroll
-        for (int i = 0; i < Q; ++i) Lanes<float2>::at(f[i], h) = c[i];
-      }
+      // both cells of the pair collide together in packed FP32
+      const float2 usq =
+          collide_v<Q, float2>(f, f, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2], S, les);
       bad |= (liq0 && !(usq.x < (float)(1.0 / 3.0))) || (liq1 && !(usq.y < (float)(1.0 / 3.0)));
       T* out = B + row + x0;
       if (liq0 && liq1) {
