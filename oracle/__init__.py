@@ -34,6 +34,7 @@ OPT_SIMPLE_FLUX = 1
 OPT_GEQ_LITERAL_NU = 2
 OPT_NEQ_LITERAL_MEAN = 4
 OPT_LAPLACE_LITERAL = 8
+OPT_BUBBLES = 16
 
 GAS, IFACE, LIQUID, OBST = 0, 1, 2, 3
 
@@ -98,6 +99,8 @@ def _load():
         lib.orc_column_height.argtypes = [P, ctypes.c_int]
         lib.orc_last_counts.argtypes = [P, ctypes.POINTER(ctypes.c_long)]
         lib.orc_get_types.argtypes = [P, ctypes.c_void_p]
+        lib.orc_get_bubbles.argtypes = [P, ctypes.c_void_p, dp]
+        lib.orc_bubble_probe.argtypes = [P, ctypes.c_void_p, dp, ctypes.c_int]
         for name in ("orc_get_pdfs", "orc_get_phi", "orc_get_mass", "orc_get_kappa"):
             getattr(lib, name).argtypes = [P, dp]
         lib.orc_normal_at.argtypes = [P, ctypes.c_long, dp]
@@ -222,6 +225,14 @@ class Oracle:
         self.lib.orc_get_phi(self.h, _dptr(out))
         return out.reshape(self._grid())
 
+    def bubbles(self):
+        """(label of every cell, -1 none; volume pressure seen by every cell),
+        each of shape (nz, ny, nx)."""
+        lab = np.empty(self.N, dtype=np.int64)
+        p = np.empty(self.N, dtype=np.float64)
+        self.lib.orc_get_bubbles(self.h, lab.ctypes.data_as(ctypes.c_void_p), _dptr(p))
+        return lab.reshape(self._grid()), p.reshape(self._grid())
+
     def mass(self):
         out = np.empty(self.N, dtype=np.float64)
         self.lib.orc_get_mass(self.h, _dptr(out))
@@ -272,6 +283,14 @@ class Oracle:
 
     def curvature_at(self, x: int) -> float:
         return float(self.lib.orc_curvature_at(self.h, int(x)))
+
+    def bubble_probe(self, types, phi, first: bool):
+        """Set types and fill levels and run only the bubble bookkeeping."""
+        types = np.ascontiguousarray(np.asarray(types, dtype=np.uint8).reshape(-1))
+        phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64).reshape(-1))
+        self.lib.orc_bubble_probe(self.h, types.ctypes.data_as(ctypes.c_void_p), _dptr(phi),
+                                  1 if first else 0)
+        return self.bubbles()
 
     def refill_probe(self, x: int, new_mask):
         new_mask = np.ascontiguousarray(np.asarray(new_mask, dtype=np.uint8).reshape(-1))

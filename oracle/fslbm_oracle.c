@@ -74,6 +74,7 @@
 #define ORC_OPT_GEQ_LITERAL_NU 2u    /* GEQ coefficient 1/(2 c_s^2 nu) as printed */
 #define ORC_OPT_NEQ_LITERAL_MEAN 4u  /* f^neq = f(y) - f^eq(rho_bar, u_bar) as printed */
 #define ORC_OPT_LAPLACE_LITERAL 8u   /* p_G = p_V - 2 sigma kappa, kappa = -div n_hat */
+#define ORC_OPT_BUBBLES 16u          /* volume pressure per enclosed gas region (bubble model) */
 
 #define CLS_STD 0
 #define CLS_NF 1 /* interface cell without liquid neighbour */
@@ -117,6 +118,12 @@ typedef struct {
   double *mex, *share;
   int *nr;
   long n_fill, n_empty, n_new;  /* conversion counts of the last step */
+  /* bubble model: label (root cell index, -1 none) of every gas and
+   * interface cell, the invariant K = p V of every bubble (kept at its root
+   * cell), the volume pressure seen by every interface cell; scratch */
+  long *blab, *bnew, *bqueue;
+  double *bK, *bKnew, *bV, *bVseen, *bp;
+  unsigned char *bhas;
 } orc_state;
 
 /* ---------------------------------------------------------------- lattice */
@@ -360,6 +367,95 @@ static void update_curvature(orc_state *s) {
 
 /* ------------------------------------------------------------ lifecycle */
 
+/* ------------------------------------------------------------ bubble model */
+
+/* Sec. 2.2, Eq. nm-fslbm-pressure-volume: an enclosed gas volume (a bubble)
+ * has the volume pressure p_V(t) = p_V(0) V(0) / V(t).  Bubbles merge and
+ * split, so (reading R23) the invariant K = p V is carried per bubble:
+ *  - bubbles are the connected components of gas cells, connected through
+ *    the 6 face neighbours (with periodic wrap); the label of a component
+ *    is its smallest cell index;
+ *  - an interface cell belongs to the bubble with the smallest label among
+ *    its gas stencil neighbours (none: no bubble, no gas PDF to rebuild);
+ *  - a bubble's volume is sum of w over its cells, w = 1 for gas and
+ *    1 - phi for interface cells;
+ *  - K of a new component = sum over old bubbles b of K_b times the share
+ *    of b's volume (w of the cells labelled b before and now in this
+ *    component, over all of b's cells still in a bubble): a bubble that only
+ *    changed volume keeps its K, merged bubbles add their K (one common
+ *    pressure), a split bubble divides its K in proportion to the volumes
+ *    (each part keeps the pressure);
+ *  - a component without any old cell starts with K = p_V V (the
+ *    configuration's volume pressure), as every bubble does initially;
+ *  - the volume pressure of an interface cell is K / V of its bubble.
+ * Sums run in cell order. */
+static void bubble_update(orc_state *s, int first) {
+  const long N = s->N;
+  const int q = s->q;
+  long *lab = s->bnew;
+  for (long x = 0; x < N; ++x) lab[x] = -1;
+  /* components of gas cells: breadth-first from the smallest unlabelled cell */
+  for (long x = 0; x < N; ++x) {
+    if (s->type[x] != ORC_GAS || lab[x] >= 0) continue;
+    long head = 0, tail = 0;
+    s->bqueue[tail++] = x;
+    lab[x] = x;
+    while (head < tail) {
+      long y = s->bqueue[head++];
+      for (int d = 1; d <= 6; ++d) {
+        long n = neighbour(s, y, d, 1);
+        if (n >= 0 && s->type[n] == ORC_GAS && lab[n] < 0) {
+          lab[n] = x;
+          s->bqueue[tail++] = n;
+        }
+      }
+    }
+  }
+  /* interface cells: smallest label among gas stencil neighbours */
+  for (long x = 0; x < N; ++x) {
+    if (s->type[x] != ORC_IFACE) continue;
+    long best = -1;
+    for (int d = 1; d < q; ++d) {
+      long n = neighbour(s, x, d, 1);
+      if (n >= 0 && s->type[n] == ORC_GAS && (best < 0 || lab[n] < best)) best = lab[n];
+    }
+    lab[x] = best;
+  }
+  for (long x = 0; x < N; ++x) {
+    s->bV[x] = 0.0;
+    s->bVseen[x] = 0.0;
+    s->bKnew[x] = 0.0;
+    s->bhas[x] = 0;
+  }
+  for (long x = 0; x < N; ++x) {
+    if (lab[x] < 0) continue;
+    double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
+    s->bV[lab[x]] += w;
+    if (!first && s->blab[x] >= 0) s->bVseen[s->blab[x]] += w;
+  }
+  if (!first) {
+    for (long x = 0; x < N; ++x) {
+      long b = s->blab[x], r = lab[x];
+      if (r < 0 || b < 0 || s->bVseen[b] == 0.0) continue;
+      double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
+      s->bKnew[r] += s->bK[b] * (w / s->bVseen[b]);
+      s->bhas[r] = 1;
+    }
+  }
+  for (long x = 0; x < N; ++x) {
+    if (lab[x] != x) continue; /* roots only */
+    if (!s->bhas[x]) s->bKnew[x] = s->c.p_v * s->bV[x];
+  }
+  for (long x = 0; x < N; ++x) {
+    s->blab[x] = lab[x];
+    s->bK[x] = (lab[x] == x) ? s->bKnew[x] : 0.0;
+  }
+  for (long x = 0; x < N; ++x) {
+    long r = s->blab[x];
+    s->bp[x] = (r >= 0 && s->bV[r] != 0.0) ? s->bK[r] / s->bV[r] : s->c.p_v;
+  }
+}
+
 void orc_destroy(orc_state *s);
 
 orc_state *orc_create(const orc_config *cfg) {
@@ -395,8 +491,19 @@ orc_state *orc_create(const orc_config *cfg) {
   s->mex = (double *)calloc(N, sizeof(double));
   s->share = (double *)calloc(N, sizeof(double));
   s->nr = (int *)calloc(N, sizeof(int));
+  s->blab = (long *)calloc(N, sizeof(long));
+  s->bnew = (long *)calloc(N, sizeof(long));
+  s->bqueue = (long *)calloc(N, sizeof(long));
+  s->bK = (double *)calloc(N, sizeof(double));
+  s->bKnew = (double *)calloc(N, sizeof(double));
+  s->bV = (double *)calloc(N, sizeof(double));
+  s->bVseen = (double *)calloc(N, sizeof(double));
+  s->bp = (double *)calloc(N, sizeof(double));
+  s->bhas = (unsigned char *)calloc(N, 1);
   if (!s->type || !s->f || !s->fn || !s->m || !s->phi || !s->rho || !s->kappa || !s->phi_t || !s->cls ||
-      !s->to_liq || !s->to_gas || !s->is_new || !s->conv || !s->mex || !s->share || !s->nr) {
+      !s->to_liq || !s->to_gas || !s->is_new || !s->conv || !s->mex || !s->share || !s->nr ||
+      !s->blab || !s->bnew || !s->bqueue || !s->bK || !s->bKnew || !s->bV || !s->bVseen || !s->bp ||
+      !s->bhas) {
     orc_destroy(s);
     return NULL;
   }
@@ -409,6 +516,8 @@ void orc_destroy(orc_state *s) {
   free(s->type); free(s->f); free(s->fn); free(s->m); free(s->phi); free(s->rho);
   free(s->kappa); free(s->phi_t); free(s->cls); free(s->to_liq); free(s->to_gas); free(s->is_new);
   free(s->conv); free(s->mex); free(s->share); free(s->nr);
+  free(s->blab); free(s->bnew); free(s->bqueue); free(s->bK); free(s->bKnew); free(s->bV);
+  free(s->bVseen); free(s->bp); free(s->bhas);
   free(s);
 }
 
@@ -459,6 +568,7 @@ int orc_init_fill(orc_state *s, const double *phi0, const double *u0, const unsi
   s->step = 0;
   s->unstable_step = -1;
   update_curvature(s);
+  if (s->c.options & ORC_OPT_BUBBLES) bubble_update(s, 1);
   return 0;
 }
 
@@ -612,8 +722,10 @@ static void step_once(orc_state *s) {
     if (iface) {
       stored_moments(s, s->f, x, &rho_t, ut);
       double pg;
-      if (s->c.options & ORC_OPT_LAPLACE_LITERAL) pg = s->c.p_v - 2.0 * s->c.sigma * s->kappa[x];
-      else pg = s->c.p_v + s->c.sigma * s->kappa[x];
+      /* Eq. nm-fslbm-pressure-volume: the bubble's volume pressure */
+      double pv = (s->c.options & ORC_OPT_BUBBLES) ? s->bp[x] : s->c.p_v;
+      if (s->c.options & ORC_OPT_LAPLACE_LITERAL) pg = pv - 2.0 * s->c.sigma * s->kappa[x];
+      else pg = pv + s->c.sigma * s->kappa[x];
       rho_g = 3.0 * pg; /* rho_G = p_G / c_s^2 */
     }
     for (int i = 0; i < q; ++i) {
@@ -823,8 +935,9 @@ static void step_once(orc_state *s) {
   s->f = s->fn;
   s->fn = tmp;
 
-  /* 6. curvature for the next step's gas density */
+  /* 6. curvature and (bubble model) volume pressure for the next step's gas density */
   update_curvature(s);
+  if (s->c.options & ORC_OPT_BUBBLES) bubble_update(s, 0);
 
   s->step += 1;
   if (unstable && s->unstable_step < 0) s->unstable_step = s->step;
@@ -856,6 +969,14 @@ void orc_last_counts(const orc_state *s, long *out3) {
 void orc_get_types(const orc_state *s, unsigned char *out) { memcpy(out, s->type, s->N); }
 void orc_get_pdfs(const orc_state *s, double *out) {
   memcpy(out, s->f, sizeof(double) * s->q * s->N);
+}
+/* bubble model: label of every cell (-1 none) and the volume pressure seen
+ * by every cell (p_V where the model is off or the cell has no bubble) */
+void orc_get_bubbles(const orc_state *s, long *lab, double *pressure) {
+  for (long x = 0; x < s->N; ++x) {
+    if (lab) lab[x] = (s->c.options & ORC_OPT_BUBBLES) ? s->blab[x] : -1;
+    if (pressure) pressure[x] = (s->c.options & ORC_OPT_BUBBLES) ? s->bp[x] : s->c.p_v;
+  }
 }
 void orc_get_phi(const orc_state *s, double *out) { memcpy(out, s->phi, sizeof(double) * s->N); }
 void orc_get_mass(const orc_state *s, double *out) { memcpy(out, s->m, sizeof(double) * s->N); }
@@ -941,6 +1062,16 @@ void orc_set_state(orc_state *s, const unsigned char *types, const double *phi, 
 /* Refill cell x with the configured scheme from the stored PDFs of its
  * neighbours, treating the cells flagged in new_mask as newly converted.
  * Writes q PDFs to out.  Used to check the schemes on hand-built cells. */
+/* Bubble bookkeeping alone, for tests: set cell types and fill levels,
+ * then run the bubble update (first = 1: fresh bubbles with K = p_V V). */
+void orc_bubble_probe(orc_state *s, const unsigned char *types, const double *phi, int first) {
+  for (long x = 0; x < s->N; ++x) {
+    s->type[x] = types[x];
+    s->phi[x] = phi[x];
+  }
+  bubble_update(s, first);
+}
+
 void orc_refill_probe(orc_state *s, long x, const unsigned char *new_mask, double *out) {
   const long N = s->N;
   memcpy(s->is_new, new_mask, s->N);

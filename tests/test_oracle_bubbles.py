@@ -1,0 +1,189 @@
+"""Pins of the oracle's bubble model (Sec. 2.2, Eq. nm-fslbm-pressure-volume:
+p_V(t) = p_V(0) V(0) / V(t) per enclosed gas volume, bubbles merging and
+splitting).  Checked against a library labelling, brute force on small
+grids, and the invariants the bookkeeping must keep: p V per bubble without
+topology change, the sum of p V through a merge, one pressure for the parts
+of a split bubble, and mass conservation with the model on."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_14496_gb300 import inputs
+
+ndimage = pytest.importorskip("scipy.ndimage")
+
+GAS, IFACE, LIQ = 0, 1, 2
+
+
+def _orc(shape, periodic=(False, False, False), p_v=1.0 / 3.0, q=19):
+    params = inputs._base(q=q, collision="srt", refill="eq", shape=shape, periodic=periodic,
+                          nu=0.05, g=(0.0, 0.0, 0.0))
+    params["options"] = oracle.OPT_BUBBLES
+    params["p_v"] = p_v
+    return oracle.Oracle(params)
+
+
+def _blobs(shape, seed):
+    """Random gas blobs in liquid with interface cells around them."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(seed)
+    gas = rng.random((nz, ny, nx)) < 0.35
+    gas = ndimage.binary_opening(gas)
+    types = np.full((nz, ny, nx), LIQ, dtype=np.uint8)
+    types[gas] = GAS
+    near = ndimage.binary_dilation(gas, structure=np.ones((3, 3, 3))) & ~gas
+    types[near] = IFACE
+    phi = np.where(types == LIQ, 1.0, np.where(types == GAS, 0.0, rng.uniform(0.05, 0.95,
+                                                                            types.shape)))
+    return types, phi
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_gas_components_match_library_labelling(seed):
+    shape = (14, 11, 9)
+    types, phi = _blobs(shape, seed)
+    o = _orc(shape)
+    lab, p = o.bubble_probe(types, phi, first=True)
+    ref, n = ndimage.label(types == GAS, structure=ndimage.generate_binary_structure(3, 1))
+    gas = types == GAS
+    # same partition, labels = smallest flat index of the component
+    flat = np.arange(types.size).reshape(types.shape)
+    for k in range(1, n + 1):
+        cells = ref == k
+        labels = np.unique(lab[cells])
+        assert labels.size == 1
+        assert labels[0] == flat[cells].min()
+    assert (lab[~gas & (types != IFACE)] == -1).all()
+    # every bubble starts at the volume pressure
+    assert np.allclose(p[gas], 1.0 / 3.0, rtol=0, atol=1e-15)
+
+
+def test_interface_cells_take_smallest_gas_neighbour_label():
+    shape = (12, 10, 8)
+    types, phi = _blobs(shape, 7)
+    o = _orc(shape, q=27)
+    lab, _ = o.bubble_probe(types, phi, first=True)
+    nz, ny, nx = types.shape
+    for z, y, x in zip(*np.nonzero(types == IFACE)):
+        best = -1
+        for dz in (-1, 0, 1):
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    zz, yy, xx = z + dz, y + dy, x + dx
+                    if (dz, dy, dx) == (0, 0, 0) or not (0 <= zz < nz and 0 <= yy < ny and 0 <= xx < nx):
+                        continue
+                    if types[zz, yy, xx] == GAS and (best < 0 or lab[zz, yy, xx] < best):
+                        best = lab[zz, yy, xx]
+        assert lab[z, y, x] == best
+
+
+def _volume(types, phi, lab, root):
+    cells = lab == root
+    return float(np.sum(np.where(types[cells] == GAS, 1.0, 1.0 - phi[cells])))
+
+
+def test_compression_keeps_pv_and_merge_adds_pv():
+    """Two bubbles, then the first compressed (its interface cells fuller),
+    then both joined by a gas bridge."""
+    shape = (16, 6, 1)
+    nz, ny, nx = 1, 6, 16
+    types = np.full((nz, ny, nx), LIQ, dtype=np.uint8)
+    phi = np.ones((nz, ny, nx))
+    types[0, 1:5, 1:5] = IFACE
+    types[0, 2:4, 2:4] = GAS
+    types[0, 1:5, 9:14] = IFACE
+    types[0, 2:4, 10:13] = GAS
+    phi[types == IFACE] = 0.5
+    phi[types == GAS] = 0.0
+    o = _orc(shape, p_v=0.3)
+    lab, p = o.bubble_probe(types, phi, first=True)
+    ra, rb = lab[0, 2, 2], lab[0, 2, 10]
+    assert ra != rb
+    Va, Vb = _volume(types, phi, lab, ra), _volume(types, phi, lab, rb)
+    Ka, Kb = 0.3 * Va, 0.3 * Vb
+    # compress bubble a: its interface cells fill to 0.8
+    phi2 = phi.copy()
+    phi2[0, 1:5, 1:5][types[0, 1:5, 1:5] == IFACE] = 0.8
+    lab2, p2 = o.bubble_probe(types, phi2, first=False)
+    Va2 = _volume(types, phi2, lab2, ra)
+    assert p2[0, 2, 2] * Va2 == pytest.approx(Ka, rel=1e-13)
+    assert p2[0, 2, 2] > 0.3
+    assert p2[0, 2, 10] == pytest.approx(0.3, rel=1e-13)
+    # bridge: gas cells join the two bubbles
+    types3 = types.copy()
+    types3[0, 2:4, 4:10] = GAS
+    types3[0, 1, 4:10] = IFACE
+    types3[0, 4, 4:10] = IFACE
+    phi3 = phi2.copy()
+    phi3[types3 == GAS] = 0.0
+    phi3[0, 1, 4:10] = 0.5
+    phi3[0, 4, 4:10] = 0.5
+    lab3, p3 = o.bubble_probe(types3, phi3, first=False)
+    r = lab3[0, 2, 2]
+    assert lab3[0, 2, 10] == r
+    V3 = _volume(types3, phi3, lab3, r)
+    # the new gas cells carry no old K: the merged bubble holds Ka + Kb
+    assert p3[0, 2, 2] * V3 == pytest.approx(Ka + Kb, rel=1e-13)
+
+
+def test_split_bubble_keeps_its_pressure_in_every_part():
+    shape = (14, 5, 1)
+    nz, ny, nx = 1, 5, 14
+    types = np.full((nz, ny, nx), LIQ, dtype=np.uint8)
+    types[0, 1:4, 1:13] = IFACE
+    types[0, 2, 2:12] = GAS
+    phi = np.where(types == IFACE, 0.4, np.where(types == GAS, 0.0, 1.0))
+    o = _orc(shape, p_v=0.25)
+    lab, p = o.bubble_probe(types, phi, first=True)
+    # compress, then cut the bubble in two with a liquid plug
+    phi2 = np.where(types == IFACE, 0.7, phi)
+    lab2, p2 = o.bubble_probe(types, phi2, first=False)
+    p_before = p2[0, 2, 2]
+    types3 = types.copy()
+    types3[0, 1:4, 7] = LIQ
+    phi3 = np.where(types3 == LIQ, 1.0, phi2)
+    lab3, p3 = o.bubble_probe(types3, phi3, first=False)
+    assert lab3[0, 2, 2] != lab3[0, 2, 10]
+    # each part keeps K in proportion to its volume: same pressure, up to the
+    # volume the plug removed (the parts' total volume is what K is spread over)
+    assert p3[0, 2, 2] == pytest.approx(p3[0, 2, 10], rel=1e-13)
+    V_all2 = _volume(types, phi2, lab2, lab2[0, 2, 2])
+    V_parts = _volume(types3, phi3, lab3, lab3[0, 2, 2]) + _volume(types3, phi3, lab3, lab3[0, 2, 10])
+    assert p3[0, 2, 2] == pytest.approx(p_before * V_all2 / V_parts, rel=1e-13)
+
+
+def test_periodic_wrap_joins_components():
+    shape = (10, 6, 1)
+    types = np.full((1, 6, 10), LIQ, dtype=np.uint8)
+    types[0, 2:4, 0:2] = GAS
+    types[0, 2:4, 8:10] = GAS
+    phi = np.where(types == GAS, 0.0, 1.0)
+    lab_open, _ = _orc(shape).bubble_probe(types, phi, first=True)
+    assert lab_open[0, 2, 0] != lab_open[0, 2, 9]
+    lab_per, _ = _orc(shape, periodic=(True, False, False)).bubble_probe(types, phi, first=True)
+    assert lab_per[0, 2, 0] == lab_per[0, 2, 9] == 20
+
+
+def test_mass_conserved_with_bubbles_through_conversions():
+    """A closed box: the gas above a sloshing column is one bubble whose
+    volume pressure follows its volume; mass stays conserved."""
+    w = inputs.dam_break(nx=40, ny=30, nz=1, width=12, height=20, g=2e-4, nu=5e-3)
+    w["params"]["periodic"] = (False, False, True)
+    w["params"]["options"] = oracle.OPT_BUBBLES
+    o = oracle.Oracle(w["params"])
+    o.init_fill(w["phi"], h_ref=w["h_ref"])
+    m0 = o.total_mass()
+    t0, phi0 = o.types(), o.phi()
+    lab0, _ = o.bubbles()
+    r0 = lab0[t0 == GAS][0]
+    K0 = (1.0 / 3.0) * _volume(t0, phi0, lab0, r0)
+    o.step(300)
+    assert abs(o.total_mass() - m0) <= 4 * 300 * np.finfo(float).eps * m0
+    lab, p = o.bubbles()
+    t, phi = o.types(), o.phi()
+    gas = t == GAS
+    assert len(np.unique(lab[gas])) == 1
+    r = lab[gas][0]
+    # one bubble through 300 steps of conversions: p V keeps its initial value
+    assert p[gas][0] * _volume(t, phi, lab, r) == pytest.approx(K0, rel=1e-12)
+    assert p[gas][0] != 1.0 / 3.0
