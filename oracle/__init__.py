@@ -101,6 +101,8 @@ def _load():
         lib.orc_get_types.argtypes = [P, ctypes.c_void_p]
         lib.orc_get_bubbles.argtypes = [P, ctypes.c_void_p, dp]
         lib.orc_bubble_probe.argtypes = [P, ctypes.c_void_p, dp, ctypes.c_int]
+        lib.orc_bubble_range_error.restype = ctypes.c_int
+        lib.orc_bubble_range_error.argtypes = [P]
         for name in ("orc_get_pdfs", "orc_get_phi", "orc_get_mass", "orc_get_kappa"):
             getattr(lib, name).argtypes = [P, dp]
         lib.orc_normal_at.argtypes = [P, ctypes.c_long, dp]
@@ -232,6 +234,10 @@ class Oracle:
         p = np.empty(self.N, dtype=np.float64)
         self.lib.orc_get_bubbles(self.h, lab.ctypes.data_as(ctypes.c_void_p), _dptr(p))
         return lab.reshape(self._grid()), p.reshape(self._grid())
+
+    def bubble_range_error(self) -> bool:
+        """True once a bubble sum term fell outside its fixed-point range."""
+        return bool(self.lib.orc_bubble_range_error(self.h))
 
     def mass(self):
         out = np.empty(self.N, dtype=np.float64)

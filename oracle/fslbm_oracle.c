@@ -122,8 +122,11 @@ typedef struct {
    * interface cell, the invariant K = p V of every bubble (kept at its root
    * cell), the volume pressure seen by every interface cell; scratch */
   long *blab, *bnew, *bqueue;
-  double *bK, *bKnew, *bV, *bVseen, *bp;
+  double *bK, *bp;
+  long long *bKnew, *bV, *bVseen; /* fixed-point sums (see bubble_update) */
   unsigned char *bhas;
+  int bub_vshift, bub_kshift; /* fixed-point scales 2^vshift, 2^kshift */
+  int bub_range;              /* a term was out of range and counted as 0 */
 } orc_state;
 
 /* ---------------------------------------------------------------- lattice */
@@ -388,11 +391,46 @@ static void update_curvature(orc_state *s) {
  *  - a component without any old cell starts with K = p_V V (the
  *    configuration's volume pressure), as every bubble does initially;
  *  - the volume pressure of an interface cell is K / V of its bubble.
- * Sums run in cell order. */
-static void bubble_update(orc_state *s, int first) {
+ * The sums are fixed-point integers, so that their value does not depend on
+ * the order of summation.  With 2^b the smallest power of two >= the cell
+ * count, each cell's w counts as round(w 2^vshift) units, vshift = 62 - b,
+ * and each share of K as round(share 2^kshift) units, kshift = vshift - 4
+ * (round to nearest, ties to even).  A sum of up to 2^b terms stays below
+ * 2^63 while |w| < 2 and every share is below 16 (a share is at most the
+ * bubble's pressure, about 1/3 in lattice units); a term outside that range
+ * counts as 0 and raises the bub_range flag, and a step in which that
+ * happens counts as unstable. */
+static void bub_scales(orc_state *s) {
+  int b = 0;
+  while ((1L << b) < s->N) ++b;
+  s->bub_vshift = 62 - b;
+  s->bub_kshift = s->bub_vshift - 4;
+}
+
+static long long bub_wq(orc_state *s, long x) {
+  double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
+  if (!(fabs(w) < 2.0)) {
+    s->bub_range = 1;
+    return 0;
+  }
+  return llrint(ldexp(w, s->bub_vshift));
+}
+
+static long long bub_kq(orc_state *s, double share) {
+  if (!(fabs(share) < 16.0)) {
+    s->bub_range = 1;
+    return 0;
+  }
+  return llrint(ldexp(share, s->bub_kshift));
+}
+
+static int bubble_update(orc_state *s, int first) {
   const long N = s->N;
   const int q = s->q;
   long *lab = s->bnew;
+  const int range_before = s->bub_range;
+  s->bub_range = 0;
+  bub_scales(s);
   for (long x = 0; x < N; ++x) lab[x] = -1;
   /* components of gas cells: breadth-first from the smallest unlabelled cell */
   for (long x = 0; x < N; ++x) {
@@ -422,38 +460,41 @@ static void bubble_update(orc_state *s, int first) {
     lab[x] = best;
   }
   for (long x = 0; x < N; ++x) {
-    s->bV[x] = 0.0;
-    s->bVseen[x] = 0.0;
-    s->bKnew[x] = 0.0;
+    s->bV[x] = 0;
+    s->bVseen[x] = 0;
+    s->bKnew[x] = 0;
     s->bhas[x] = 0;
   }
   for (long x = 0; x < N; ++x) {
     if (lab[x] < 0) continue;
-    double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
-    s->bV[lab[x]] += w;
-    if (!first && s->blab[x] >= 0) s->bVseen[s->blab[x]] += w;
+    long long wq = bub_wq(s, x);
+    s->bV[lab[x]] += wq;
+    if (!first && s->blab[x] >= 0) s->bVseen[s->blab[x]] += wq;
   }
   if (!first) {
     for (long x = 0; x < N; ++x) {
       long b = s->blab[x], r = lab[x];
-      if (r < 0 || b < 0 || s->bVseen[b] == 0.0) continue;
-      double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
-      s->bKnew[r] += s->bK[b] * (w / s->bVseen[b]);
+      if (r < 0 || b < 0 || s->bVseen[b] == 0) continue;
+      double share = s->bK[b] * ((double)bub_wq(s, x) / (double)s->bVseen[b]);
+      s->bKnew[r] += bub_kq(s, share);
       s->bhas[r] = 1;
     }
   }
   for (long x = 0; x < N; ++x) {
-    if (lab[x] != x) continue; /* roots only */
-    if (!s->bhas[x]) s->bKnew[x] = s->c.p_v * s->bV[x];
-  }
-  for (long x = 0; x < N; ++x) {
-    s->blab[x] = lab[x];
-    s->bK[x] = (lab[x] == x) ? s->bKnew[x] : 0.0;
+    long r = lab[x];
+    s->blab[x] = r;
+    double V = (r >= 0) ? ldexp((double)s->bV[r], -s->bub_vshift) : 0.0;
+    if (r == x) s->bK[x] = s->bhas[x] ? ldexp((double)s->bKnew[x], -s->bub_kshift) : s->c.p_v * V;
+    else s->bK[x] = 0.0;
   }
   for (long x = 0; x < N; ++x) {
     long r = s->blab[x];
-    s->bp[x] = (r >= 0 && s->bV[r] != 0.0) ? s->bK[r] / s->bV[r] : s->c.p_v;
+    double V = (r >= 0) ? ldexp((double)s->bV[r], -s->bub_vshift) : 0.0;
+    s->bp[x] = (r >= 0 && V != 0.0) ? s->bK[r] / V : s->c.p_v;
   }
+  const int out = s->bub_range;
+  s->bub_range |= range_before;
+  return out;
 }
 
 void orc_destroy(orc_state *s);
@@ -495,9 +536,9 @@ orc_state *orc_create(const orc_config *cfg) {
   s->bnew = (long *)calloc(N, sizeof(long));
   s->bqueue = (long *)calloc(N, sizeof(long));
   s->bK = (double *)calloc(N, sizeof(double));
-  s->bKnew = (double *)calloc(N, sizeof(double));
-  s->bV = (double *)calloc(N, sizeof(double));
-  s->bVseen = (double *)calloc(N, sizeof(double));
+  s->bKnew = (long long *)calloc(N, sizeof(long long));
+  s->bV = (long long *)calloc(N, sizeof(long long));
+  s->bVseen = (long long *)calloc(N, sizeof(long long));
   s->bp = (double *)calloc(N, sizeof(double));
   s->bhas = (unsigned char *)calloc(N, 1);
   if (!s->type || !s->f || !s->fn || !s->m || !s->phi || !s->rho || !s->kappa || !s->phi_t || !s->cls ||
@@ -937,7 +978,7 @@ static void step_once(orc_state *s) {
 
   /* 6. curvature and (bubble model) volume pressure for the next step's gas density */
   update_curvature(s);
-  if (s->c.options & ORC_OPT_BUBBLES) bubble_update(s, 0);
+  if ((s->c.options & ORC_OPT_BUBBLES) && bubble_update(s, 0)) unstable = 1;
 
   s->step += 1;
   if (unstable && s->unstable_step < 0) s->unstable_step = s->step;
@@ -1064,6 +1105,8 @@ void orc_set_state(orc_state *s, const unsigned char *types, const double *phi, 
  * Writes q PDFs to out.  Used to check the schemes on hand-built cells. */
 /* Bubble bookkeeping alone, for tests: set cell types and fill levels,
  * then run the bubble update (first = 1: fresh bubbles with K = p_V V). */
+int orc_bubble_range_error(const orc_state *s) { return s->bub_range; }
+
 void orc_bubble_probe(orc_state *s, const unsigned char *types, const double *phi, int first) {
   for (long x = 0; x < s->N; ++x) {
     s->type[x] = types[x];
