@@ -74,7 +74,11 @@ enum {
   FSL_OPT_SIMPLE_FLUX = 1u,      /* plain Eq. nm-fslbm-mass-flux, no Thuerey table */
   FSL_OPT_GEQ_LITERAL_NU = 2u,   /* GEQ prefactor 1/(2 c_s^2 nu) as printed (default 1/(2 c_s^2 omega)) */
   FSL_OPT_NEQ_LITERAL_MEAN = 4u, /* EQ+NEQ: f_i(y) - f_i^eq(rho_bar, u_bar) as printed */
-  FSL_OPT_LAPLACE_LITERAL = 8u   /* p_G = p_V - 2 sigma kappa (default p_G = p_V + sigma K) */
+  FSL_OPT_LAPLACE_LITERAL = 8u,  /* p_G = p_V - 2 sigma kappa (default p_G = p_V + sigma K) */
+  FSL_OPT_BUBBLES = 16u          /* bubble model (Sec. 2.2, Eq. nm-fslbm-pressure-volume):
+                                    every face-connected gas region has its own volume
+                                    pressure p_V(0) V(0)/V(t), p V carried through merges
+                                    and splits; p_volume is the initial pressure */
 };
 
 typedef struct {
@@ -142,7 +146,11 @@ enum {
   FSL_OBS_FIELD_TYPES = 17,  /* uint8[N]: 0 gas, 1 interface, 2 liquid, 3 obstacle */
   FSL_OBS_FIELD_PHI = 18,    /* double[N]: fill level */
   FSL_OBS_FIELD_MASS = 19,   /* double[N]: cell mass m (meaningful in interface cells) */
-  FSL_OBS_FIELD_KAPPA = 20   /* double[N]: curvature K = -div(n_hat) (interface cells, sigma != 0) */
+  FSL_OBS_FIELD_KAPPA = 20,  /* double[N]: curvature K = -div(n_hat) (interface cells, sigma != 0) */
+  FSL_OBS_FIELD_BUBBLE = 21, /* int32[N]: bubble of each gas or interface cell (dense index of
+                                the bubble's smallest cell), -1 none or model off */
+  FSL_OBS_FIELD_PRESSURE = 22 /* double[N]: volume pressure seen by each cell (p_volume where
+                                the model is off or the cell has no bubble) */
 };
 /* Reads an observable into host memory; synchronises the stream.
  * FSL_ERR_ARG if `bytes` is smaller than the observable. FSL_OBS_TRACE holds
@@ -279,7 +287,8 @@ fsl_status fsl_batch_destroy(fsl_batch* b);
  * initial state.  The paper has no adjoint; this is the differentiation
  * pattern built around its method.  Scope: FP64 or FP32 storage, SRT, EQ
  * refilling, no surface tension, no turbulence model, no-slip walls or
- * periodic faces, no interior obstacles (FSL_ERR_ARG otherwise).  Cell types
+ * periodic faces, no interior obstacles, no bubble model (FSL_ERR_ARG
+ * otherwise).  Cell types
  * and every conversion decision of the forward run are replayed, so the
  * gradient is that of the step map with those decisions fixed (the usual
  * discrete adjoint of a free-surface scheme); the stream-collide, the

@@ -36,7 +36,8 @@ constexpr long long kPlaneSkew = 512;  // elements added to every PDF plane
 
 enum Region {
   R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST,
-  R_LIF, R_LIF2, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_LTILES, R_CTRL, R_TRACE, R_RED, R_COUNT
+  R_LIF, R_LIF2, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_LTILES, R_CTRL, R_TRACE, R_RED,
+  R_BLAB, R_BNEW, R_BK, R_BKNEW, R_BV, R_BVSEEN, R_BP, R_BHAS, R_COUNT
 };
 
 bool valid_config(const fsl_config* c) {
@@ -75,6 +76,7 @@ void make_geom(const fsl_config* c, Geom* g) {
   g->has_obst = 0;
   g->variant = FSL_VARIANT_DEFAULT;
   g->free_slip = 0;
+  g->bubbles = (c->options & FSL_OPT_BUBBLES) ? 1 : 0;
   for (int a = 0; a < 3; ++a)
     if (c->free_slip[a] && !c->periodic[a]) g->free_slip |= 1 << a;
 }
@@ -136,6 +138,12 @@ void region_sizes(const fsl_config* c, const Geom& g, size_t* sz) {
   // tile lists of the shared-memory variants: up to one entry per 64 cells of a row
   sz[R_LTILES] = (size_t)((g.nx + 63) / 64) * g.ny * g.nz * sizeof(int);
   sz[R_CTRL] = sizeof(Ctrl);
+  {
+    const size_t bc = (c->options & FSL_OPT_BUBBLES) ? cells : 0;
+    sz[R_BLAB] = sz[R_BNEW] = bc * sizeof(int);
+    sz[R_BK] = sz[R_BKNEW] = sz[R_BV] = sz[R_BVSEEN] = sz[R_BP] = bc * 8;
+    sz[R_BHAS] = bc;
+  }
   sz[R_TRACE] = (size_t)kTraceCapacity * 3 * sizeof(double);
   sz[R_RED] = (size_t)(2 * kReduceBlocks + 16) * sizeof(double);
 }
@@ -321,6 +329,14 @@ fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, vo
   d.l_recv = reinterpret_cast<int*>(base + h->off[R_LRECV]);
   d.l_tiles = reinterpret_cast<int*>(base + h->off[R_LTILES]);
   d.ctrl = reinterpret_cast<Ctrl*>(base + h->off[R_CTRL]);
+  d.blab = reinterpret_cast<int*>(base + h->off[R_BLAB]);
+  d.bnew = reinterpret_cast<int*>(base + h->off[R_BNEW]);
+  d.bK = reinterpret_cast<double*>(base + h->off[R_BK]);
+  d.bKnew = reinterpret_cast<long long*>(base + h->off[R_BKNEW]);
+  d.bV = reinterpret_cast<long long*>(base + h->off[R_BV]);
+  d.bVseen = reinterpret_cast<long long*>(base + h->off[R_BVSEEN]);
+  d.bp = reinterpret_cast<double*>(base + h->off[R_BP]);
+  d.bhas = reinterpret_cast<uint8_t*>(base + h->off[R_BHAS]);
   d.trace = reinterpret_cast<double*>(base + h->off[R_TRACE]);
   d.red = reinterpret_cast<double*>(base + h->off[R_RED]);
   d.redi = nullptr;
@@ -519,6 +535,29 @@ fsl_status fsl_observe(fsl_handle* h, int what, void* host_out, size_t bytes) {
     case FSL_OBS_FIELD_KAPPA:
       if (bytes < n * sizeof(double)) return FSL_ERR_ARG;
       return copy_field(h, h->d.kappa, sizeof(double), host_out);
+    case FSL_OBS_FIELD_BUBBLE: {
+      if (bytes < n * sizeof(int)) return FSL_ERR_ARG;
+      int* o = static_cast<int*>(host_out);
+      if (!h->g.bubbles) {
+        for (size_t k = 0; k < n; ++k) o[k] = -1;
+        return FSL_OK;
+      }
+      fsl_status st2 = copy_field(h, h->d.blab, sizeof(int), host_out);
+      if (st2 != FSL_OK) return st2;
+      // padded cell index -> dense index x + nx (y + ny z)
+      for (size_t k = 0; k < n; ++k)
+        if (o[k] >= 0) o[k] = (o[k] % h->g.sx) + h->g.nx * (o[k] / h->g.sx);
+      return FSL_OK;
+    }
+    case FSL_OBS_FIELD_PRESSURE: {
+      if (bytes < n * sizeof(double)) return FSL_ERR_ARG;
+      if (!h->g.bubbles) {
+        double* o = static_cast<double*>(host_out);
+        for (size_t k = 0; k < n; ++k) o[k] = h->p.p_v;
+        return FSL_OK;
+      }
+      return copy_field(h, h->d.bp, sizeof(double), host_out);
+    }
   }
   return FSL_ERR_ARG;
 }
@@ -540,7 +579,8 @@ fsl_status fsl_state_bytes(const fsl_handle* h, size_t* bytes) {
   if (!h || !bytes) return FSL_ERR_ARG;
   size_t sz[R_COUNT];
   region_sizes(&h->cfg, h->g, sz);
-  *bytes = sz[R_PDF0] + sz[R_FLAGS] + sz[R_PHI] + sz[R_MASS] + sz[R_KAPPA] + sz[R_LOST] + sizeof(Ctrl);
+  *bytes = sz[R_PDF0] + sz[R_FLAGS] + sz[R_PHI] + sz[R_MASS] + sz[R_KAPPA] + sz[R_LOST] +
+           sz[R_BLAB] + sz[R_BK] + sz[R_BP] + sizeof(Ctrl);
   return FSL_OK;
 }
 
@@ -554,6 +594,11 @@ static fsl_status state_parts(fsl_handle* h, int cur, std::vector<std::pair<char
   parts.push_back({reinterpret_cast<char*>(h->d.mass), sz[R_MASS]});
   parts.push_back({reinterpret_cast<char*>(h->d.kappa), sz[R_KAPPA]});
   parts.push_back({reinterpret_cast<char*>(h->d.lost), sz[R_LOST]});
+  if (h->g.bubbles) {
+    parts.push_back({reinterpret_cast<char*>(h->d.blab), sz[R_BLAB]});
+    parts.push_back({reinterpret_cast<char*>(h->d.bK), sz[R_BK]});
+    parts.push_back({reinterpret_cast<char*>(h->d.bp), sz[R_BP]});
+  }
   return FSL_OK;
 }
 
@@ -661,7 +706,7 @@ bool adjoint_supported(const fsl_handle* h) {
   const fsl_config& c = h->cfg;
   return (c.precision == FSL_FP64 || c.precision == FSL_FP32) && c.collision == FSL_SRT &&
          c.refill == FSL_REFILL_EQ && c.sigma == 0.0 && c.les_cs == 0.0 && h->g.free_slip == 0 &&
-         h->g.has_obst == 0;
+         h->g.has_obst == 0 && h->g.bubbles == 0;
 }
 
 size_t adjoint_layout(const fsl_handle* h, int nsteps, int every, size_t* off) {

@@ -34,7 +34,8 @@ struct Ctrl {
   unsigned last[4];    // previous step: filled, emptied (after conflicts), new, interface
   int trace_every;     // 0: no trace
   int trace_count;     // records written (ring index = count % capacity)
-  unsigned timeout;    // error bits: 1 CAS retry cap, 2 refill without source, 4 copy wait gave up
+  unsigned timeout;    // error bits: 1 CAS retry cap, 2 refill without source, 4 copy wait gave up,
+                       // 8 bubble union retry cap
   unsigned n_emptied;  // to-gas cells actually converted this step
   unsigned end_blocks; // end-of-step blocks finished
   unsigned n_tiles;    // tiles holding liquid cells, listed this step (16/32-bit path)
@@ -58,6 +59,7 @@ struct Geom {
   int has_obst;        // the initial state had interior obstacle cells
   int free_slip;       // bit a: the walls of non-periodic axis a are free-slip (specular)
   int variant;         // bulk kernel of the 16/32-bit path (FSL_VARIANT_*; 0 = default)
+  int bubbles;         // bubble model on (FSL_OPT_BUBBLES)
 };
 
 struct Phys {
@@ -106,6 +108,17 @@ struct Dev {
   double* trace;      // kTraceCapacity * 3 doubles
   double* red;        // reduction scratch, kReduceBlocks * 2 doubles
   int* redi;          // integer reduction scratch
+  // bubble model (empty when off): label per cell and its next value, K = p V
+  // per bubble root and its next value, volumes, volume pressure per cell;
+  // the next K and the volumes are fixed-point sums
+  int* blab;
+  int* bnew;
+  double* bK;
+  long long* bKnew;
+  long long* bV;
+  long long* bVseen;
+  double* bp;
+  uint8_t* bhas;
 };
 
 // Per-precision-family launch table, implemented in fsl_prec_*.cu.

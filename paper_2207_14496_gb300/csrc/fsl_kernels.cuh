@@ -863,6 +863,7 @@ __global__ void __launch_bounds__(128, 3) k_stream_collide_pp(Dev d, Geom g, Phy
 
 }  // namespace fsl
 #include "fsl_bulk.cuh"
+#include "fsl_bubble.cuh"
 namespace fsl {
 
 // ------------------------------------------------------------ stream-collide
@@ -934,8 +935,11 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
     const R uty = jy / rt - (R)0.5 * PAR(R, p, g[1]);
     const R utz = jz / rt - (R)0.5 * PAR(R, p, g[2]);
     const R utsq = utx * utx + uty * uty + utz * utz;
-    const double pg = (p.options & 8u) ? p.p_v - 2.0 * p.sigma * d.kappa[c]
-                                       : p.p_v + p.sigma * d.kappa[c];
+    // Eq. nm-fslbm-pressure-gas: volume pressure (per bubble with the bubble
+    // model, Eq. nm-fslbm-pressure-volume) and Laplace pressure
+    const double pv = g.bubbles ? d.bp[c] : p.p_v;
+    const double pg = (p.options & 8u) ? pv - 2.0 * p.sigma * d.kappa[c]
+                                       : pv + p.sigma * d.kappa[c];
     const R rg = (R)(3.0 * pg);  // rho_G = p_G / c_s^2
     const R drg = (R)(3.0 * pg - 1.0);
     R feg[Q];
@@ -2003,6 +2007,10 @@ struct Kernels {
     k_refill<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
     k_excess_share<Q><<<kListBlocks, 256, 0, s>>>(d, g);
     k_excess_gather<Q><<<kListBlocks, 256, 0, s>>>(d, g);
+    if (g.bubbles) {
+      e = bubble_update<Q>(d, g, p, 0, s);
+      if (e != cudaSuccess) return e;
+    }
     k_classify<Q, ST><<<kCellListBlocks, 128, 0, s>>>(d, g, p);
     k_end_step<<<kEndBlocks, 256, 0, s>>>(d, g);
     return cudaGetLastError();
@@ -2016,6 +2024,7 @@ struct Kernels {
     k_init_state<Q, ST><<<blocks, 256, 0, s>>>(d, g, p, cur, u0, h_ref);
     k_init_classes<Q, ST><<<blocks, 128, 0, s>>>(d, g, p);
     k_list_interface<<<blocks, 256, 0, s>>>(d, g);
+    if (g.bubbles) return bubble_update<Q>(d, g, p, 1, s);
     return cudaGetLastError();
   }
   static cudaError_t total_mass(const Dev& d, const Geom& g, const Phys&, int cur, double* out,
@@ -2134,8 +2143,9 @@ struct Kernels {
     return cudaGetLastError();
   }
   static int launches(const Geom& g) {
-    if constexpr (ST::kShift) return (variant_of(g) == 4 || variant_of(g) == 6) ? 12 : 11;
-    return 11;
+    const int bub = g.bubbles ? 8 : 0;
+    if constexpr (ST::kShift) return ((variant_of(g) == 4 || variant_of(g) == 6) ? 12 : 11) + bub;
+    return 11 + bub;
   }
   static const Launch* table() {
     static const Launch L = {&step, &init, &total_mass, &max_velocity, &export_pdf,

@@ -34,6 +34,8 @@ OBS_TOTAL_MASS, OBS_COLUMN_HEIGHT, OBS_FRONT, OBS_HEIGHT = 1, 2, 3, 4
 OBS_MAX_VELOCITY, OBS_STATUS, OBS_STEP, OBS_COUNTS = 5, 6, 7, 8
 OBS_LOST_MASS, OBS_TRACE = 9, 10
 OBS_FIELD_PDF, OBS_FIELD_TYPES, OBS_FIELD_PHI, OBS_FIELD_MASS, OBS_FIELD_KAPPA = 16, 17, 18, 19, 20
+OBS_FIELD_BUBBLE, OBS_FIELD_PRESSURE = 21, 22
+OPT_BUBBLES = 16
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace", -4: "unstable",
           -5: "timeout", -6: "state"}
@@ -327,6 +329,14 @@ class Sim:
 
     def kappa(self):
         return self._obs(OBS_FIELD_KAPPA, np.zeros(self.N)).reshape(self._grid())
+
+    def bubbles(self):
+        """Bubble of every cell (dense index of its smallest cell, -1 none)."""
+        return self._obs(OBS_FIELD_BUBBLE, np.zeros(self.N, dtype=np.int32)).reshape(self._grid())
+
+    def pressure(self):
+        """Volume pressure seen by every cell."""
+        return self._obs(OBS_FIELD_PRESSURE, np.zeros(self.N)).reshape(self._grid())
 
     # -- checkpoint -------------------------------------------------------------
     def save(self) -> np.ndarray:

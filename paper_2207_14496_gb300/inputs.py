@@ -203,6 +203,25 @@ def drop_impact(n=256, pool=96, diameter=40.0, gap=30.0, speed=0.05, sigma=1e-4,
                 obstacle=None, h_ref=float(pool))
 
 
+def bubbles_in_pool(nx=48, ny=40, depth=32, bubbles=((12.0, 9.0, 4.5), (30.0, 13.0, 5.5),
+                                                      (21.0, 21.0, 4.0)), g=2e-4, nu=5e-3,
+                    q=19, collision="trt", refill="eq"):
+    """Enclosed gas bubbles (discs (x, y, radius)) in a pool of depth `depth`
+    under a gas layer, nx x ny x 1, periodic x and z, walls in y, gravity -y,
+    with the bubble model on (each bubble keeps its own volume pressure)."""
+    phi = np.zeros((1, ny, nx))
+    phi[0, :depth, :] = 1.0
+    if depth < ny:
+        phi[0, depth, :] = 0.0
+    for cx, cy, r in bubbles:
+        phi -= cylinder_fraction(nx, ny, (cx, cy), r)
+    phi = np.clip(phi, 0.0, 1.0)
+    params = _base(q=q, collision=collision, refill=refill, shape=(nx, ny, 1),
+                   periodic=(True, False, True), nu=nu, g=(0.0, -g, 0.0), options=16)
+    return dict(name=f"bubbles_in_pool_{nx}x{ny}", params=params, phi=phi, u0=None,
+                obstacle=None, h_ref=float(depth))
+
+
 def static_drop(n=32, radius=8.0, sigma=1e-3, nu=0.1, q=19, two_d=False):
     """Resting drop in a fully periodic box without gravity (Young-Laplace)."""
     if two_d:
