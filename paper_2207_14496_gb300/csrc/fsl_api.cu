@@ -556,7 +556,12 @@ fsl_status fsl_observe(fsl_handle* h, int what, void* host_out, size_t bytes) {
         for (size_t k = 0; k < n; ++k) o[k] = h->p.p_v;
         return FSL_OK;
       }
-      return copy_field(h, h->d.bp, sizeof(double), host_out);
+      // the pressure lives at each bubble's root: expand it per cell into the
+      // next-K scratch, which the next step re-initialises anyway
+      double* tmp = reinterpret_cast<double*>(h->d.bKnew);
+      k_bub_expand<<<4 * 152, 256, 0, h->stream>>>(h->d, h->g, h->p.p_v, tmp);
+      FSL_CK(cudaGetLastError());
+      return copy_field(h, tmp, sizeof(double), host_out);
     }
   }
   return FSL_ERR_ARG;

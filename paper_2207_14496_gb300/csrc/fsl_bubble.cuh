@@ -12,7 +12,8 @@
 //     interface cell; its new K is the sum, over the cells it holds that
 //     were in a bubble b before, of K_b times the cell's share of b's volume
 //     still in bubbles; a bubble with no such cell starts at K = p_V V;
-//   - interface cells see the volume pressure K / V of their bubble.
+//   - interface cells see the volume pressure K / V of their bubble, kept
+//     at the bubble's root cell (bp) and read through the cell's label.
 // The sums are fixed-point integers, so their value does not depend on the
 // order in which the atomics land: with 2^b the smallest power of two not
 // below nx*ny*nz, a cell's volume term w counts as round(w 2^vshift) units,
@@ -102,15 +103,20 @@ __device__ __forceinline__ long long bub_wq(const Dev& d, int c, double vs, bool
   return __double2ll_rn(w * vs);
 }
 
-static __global__ void k_bub_init(Dev d, Geom g) {
+// every gas cell its own root; clear the sums of the new roots (gas cells)
+// and the seen volume of the old roots
+static __global__ void k_bub_init(Dev d, Geom g, int first) {
   FSL_GRID_LOOP(k, (unsigned)g.cells) {
     const int c = (int)k;
     const int x = c % g.sx;
-    d.bnew[c] = (x < g.nx && (d.flags[c] & F_TYPE) == T_GAS) ? c : -1;
-    d.bV[c] = 0;
-    d.bVseen[c] = 0;
-    d.bKnew[c] = 0;
-    d.bhas[c] = 0;
+    const bool gas = x < g.nx && (d.flags[c] & F_TYPE) == T_GAS;
+    d.bnew[c] = gas ? c : -1;
+    if (gas) {
+      d.bV[c] = 0;
+      d.bKnew[c] = 0;
+      d.bhas[c] = 0;
+    }
+    if (!first && d.blab[c] == c) d.bVseen[c] = 0;
   }
 }
 
@@ -132,29 +138,31 @@ static __global__ void k_bub_union(Dev d, Geom g) {
   }
 }
 
-static __global__ void k_bub_flatten(Dev d, Geom g) {
-  FSL_GRID_LOOP(k, (unsigned)g.cells) {
-    const int c = (int)k;
-    if (d.bnew[c] >= 0) d.bnew[c] = bub_find(d.bnew, c);
-  }
-}
-
+// gas cells point straight at their root; an interface cell takes the
+// smallest root among its gas stencil neighbours.  Concurrent finds stay
+// valid: flattening only ever stores a cell's root, and interface cells are
+// on no gas cell's path.
 template <int Q>
-__global__ void k_bub_iface(Dev d, Geom g) {
+__global__ void k_bub_label(Dev d, Geom g) {
   FSL_GRID_LOOP(k, (unsigned)g.cells) {
     const int c = (int)k;
     int x, y, z;
     cell_xyz(g, c, x, y, z);
-    if (x >= g.nx || (d.flags[c] & F_TYPE) != T_IF) continue;
-    int best = -1;
-    for (int i = 1; i < Q; ++i) {
-      const int n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
-      if (n >= 0 && (d.flags[n] & F_TYPE) == T_GAS) {
-        const int l = d.bnew[n];
-        if (best < 0 || l < best) best = l;
+    if (x >= g.nx) continue;
+    const uint8_t t = d.flags[c] & F_TYPE;
+    if (t == T_GAS) {
+      d.bnew[c] = bub_find(d.bnew, c);
+    } else if (t == T_IF) {
+      int best = -1;
+      for (int i = 1; i < Q; ++i) {
+        const int n = nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2));
+        if (n >= 0 && (d.flags[n] & F_TYPE) == T_GAS) {
+          const int l = bub_find(d.bnew, n);
+          if (best < 0 || l < best) best = l;
+        }
       }
+      d.bnew[c] = best;
     }
-    d.bnew[c] = best;
   }
 }
 
@@ -206,26 +214,28 @@ static __global__ void k_bub_kmap(Dev d, Geom g, double vs, double ks) {
   }
 }
 
-// K of every bubble at its root: the carried sum, or p_V V for a bubble
-// without a predecessor; 0 at every other cell
-static __global__ void k_bub_kroot(Dev d, Geom g, double p_v, double vinv, double kinv) {
-  FSL_GRID_LOOP(k, (unsigned)g.cells) {
-    const int c = (int)k;
-    const int r = d.bnew[c];
-    double K = 0.0;
-    if (r == c) K = d.bhas[c] ? (double)d.bKnew[c] * kinv : p_v * ((double)d.bV[c] * vinv);
-    d.bK[c] = K;
-  }
-}
-
-// the new labels become the state; volume pressure of every cell
-static __global__ void k_bub_commit(Dev d, Geom g, double p_v, double vinv) {
+// the new labels become the state; K and volume pressure of every bubble at
+// its root: the carried sum of K, or p_V V for a bubble without a predecessor
+static __global__ void k_bub_commit(Dev d, Geom g, double p_v, double vinv, double kinv) {
   FSL_GRID_LOOP(k, (unsigned)g.cells) {
     const int c = (int)k;
     const int r = d.bnew[c];
     d.blab[c] = r;
-    const double V = r >= 0 ? (double)d.bV[r] * vinv : 0.0;
-    d.bp[c] = (r >= 0 && V != 0.0) ? d.bK[r] / V : p_v;
+    if (r == c) {
+      const double V = (double)d.bV[c] * vinv;
+      const double K = d.bhas[c] ? (double)d.bKnew[c] * kinv : p_v * V;
+      d.bK[c] = K;
+      d.bp[c] = V != 0.0 ? K / V : p_v;
+    }
+  }
+}
+
+// volume pressure of every cell (the bubble's, else p_V) into out
+static __global__ void k_bub_expand(Dev d, Geom g, double p_v, double* out) {
+  FSL_GRID_LOOP(k, (unsigned)g.cells) {
+    const int c = (int)k;
+    const int r = d.blab[c];
+    out[c] = r >= 0 ? d.bp[r] : p_v;
   }
 }
 
@@ -234,14 +244,12 @@ template <int Q>
 cudaError_t bubble_update(const Dev& d, const Geom& g, const Phys& p, int first, cudaStream_t s) {
   const int blocks = 4 * 152;
   const BubScale sc = bub_scale(g);
-  k_bub_init<<<blocks, 256, 0, s>>>(d, g);
+  k_bub_init<<<blocks, 256, 0, s>>>(d, g, first);
   k_bub_union<<<blocks, 256, 0, s>>>(d, g);
-  k_bub_flatten<<<blocks, 256, 0, s>>>(d, g);
-  k_bub_iface<Q><<<blocks, 256, 0, s>>>(d, g);
+  k_bub_label<Q><<<blocks, 256, 0, s>>>(d, g);
   k_bub_volume<<<blocks, 256, 0, s>>>(d, g, first, sc.vs);
   if (!first) k_bub_kmap<<<blocks, 256, 0, s>>>(d, g, sc.vs, sc.ks);
-  k_bub_kroot<<<blocks, 256, 0, s>>>(d, g, p.p_v, sc.vinv, sc.kinv);
-  k_bub_commit<<<blocks, 256, 0, s>>>(d, g, p.p_v, sc.vinv);
+  k_bub_commit<<<blocks, 256, 0, s>>>(d, g, p.p_v, sc.vinv, sc.kinv);
   return cudaGetLastError();
 }
 

@@ -109,8 +109,8 @@ struct Dev {
   double* red;        // reduction scratch, kReduceBlocks * 2 doubles
   int* redi;          // integer reduction scratch
   // bubble model (empty when off): label per cell and its next value, K = p V
-  // per bubble root and its next value, volumes, volume pressure per cell;
-  // the next K and the volumes are fixed-point sums
+  // and volume pressure per bubble (at its root cell), the next K and the
+  // volumes as fixed-point sums
   int* blab;
   int* bnew;
   double* bK;

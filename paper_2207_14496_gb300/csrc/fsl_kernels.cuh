@@ -482,7 +482,10 @@ __global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, P
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  const int y = blockIdx.y, z = blockIdx.z;
+  // narrow domains put several rows in one block (blockDim.x is a multiple
+  // of 32, so every warp lies in one row)
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  if (y >= g.ny) return;
   const int row = g.sx * (y + g.ny * z);
   const bool in_row = x0 < g.sx;
   const int xc = in_row ? x0 : g.sx - 2;  // clamped pair start for addressing
@@ -937,7 +940,9 @@ __global__ void __launch_bounds__(128) k_stream_collide_if(Dev d, Geom g, Phys p
     const R utsq = utx * utx + uty * uty + utz * utz;
     // Eq. nm-fslbm-pressure-gas: volume pressure (per bubble with the bubble
     // model, Eq. nm-fslbm-pressure-volume) and Laplace pressure
-    const double pv = g.bubbles ? d.bp[c] : p.p_v;
+    int bub = -1;
+    if (g.bubbles) bub = d.blab[c];
+    const double pv = bub >= 0 ? d.bp[bub] : p.p_v;
     const double pg = (p.options & 8u) ? pv - 2.0 * p.sigma * d.kappa[c]
                                        : pv + p.sigma * d.kappa[c];
     const R rg = (R)(3.0 * pg);  // rho_G = p_G / c_s^2
@@ -2123,18 +2128,21 @@ struct Kernels {
           dim3 b1(64), g1((g.nx + 255) / 256, g.ny, g.nz);
           k_stream_collide_lp4<Q, ST><<<g1, b1, 0, s>>>(d, g, p);
         }
-      } else if (v == 1) {
-        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
-        k_stream_collide_lp<Q, ST, 128, 4, true><<<g1, b1, 0, s>>>(d, g, p);
-      } else if (v == 2) {
-        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
-        k_stream_collide_lp<Q, ST, 128, 4, false><<<g1, b1, 0, s>>>(d, g, p);
-      } else if (v == 3) {
-        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
-        k_stream_collide_lp<Q, ST, 128, 5, true><<<g1, b1, 0, s>>>(d, g, p);
       } else {
-        dim3 b1(128), g1((g.nx + 255) / 256, g.ny, g.nz);
-        k_stream_collide_lp<Q, ST, 128, 6, true><<<g1, b1, 0, s>>>(d, g, p);
+        // 128 threads, two cells each: rows of up to 256 cells take one warp
+        // row per 64 cells, and narrower domains stack rows in the block
+        const int half = (g.nx + 1) / 2;
+        const int bx = half >= 128 ? 128 : ((half + 31) / 32) * 32;
+        const int by = 128 / bx;
+        dim3 b1(bx, by), g1((g.nx + 2 * bx - 1) / (2 * bx), (g.ny + by - 1) / by, g.nz);
+        if (v == 1)
+          k_stream_collide_lp<Q, ST, 128, 4, true><<<g1, b1, 0, s>>>(d, g, p);
+        else if (v == 2)
+          k_stream_collide_lp<Q, ST, 128, 4, false><<<g1, b1, 0, s>>>(d, g, p);
+        else if (v == 3)
+          k_stream_collide_lp<Q, ST, 128, 5, true><<<g1, b1, 0, s>>>(d, g, p);
+        else
+          k_stream_collide_lp<Q, ST, 128, 6, true><<<g1, b1, 0, s>>>(d, g, p);
       }
     } else {
       dim3 b1(128), g1((g.nx + 127) / 128, g.ny, g.nz);
@@ -2143,7 +2151,7 @@ struct Kernels {
     return cudaGetLastError();
   }
   static int launches(const Geom& g) {
-    const int bub = g.bubbles ? 8 : 0;
+    const int bub = g.bubbles ? 6 : 0;
     if constexpr (ST::kShift) return ((variant_of(g) == 4 || variant_of(g) == 6) ? 12 : 11) + bub;
     return 11 + bub;
   }

@@ -4,6 +4,15 @@
 Smagorinsky model, W in {50, 100, 200}) and reports the residual height and
 front position over time and any instability.
 
+`taylor_bubble` runs the Taylor bubble of Sec. 4.4 (D in {32, 64, 128},
+bubble model on) and reports the Reynolds number of the rise velocity taken
+from the bubble's centre of mass at t* = 10 and t* = 15, beside the paper's
+printed values.
+
+`bubbly_poiseuille` runs the bubbly plane Poiseuille flow of Sec. 4.6 (381
+bubbles in a force-driven channel) and reports how the bubbles gather and
+coalesce and which schemes go unstable.
+
 `batched_waves` runs the set of 320 small independent wave domains as one
 batch and as one launch per domain.
 
@@ -153,6 +162,120 @@ def dam_break(W: int, scheme: str, precision: str = "fp64", t_end: float = 3.5,
     return out
 
 
+# Reynolds numbers printed in Sec. 4.4 (table of the Taylor bubble) per D
+PAPER_TAYLOR_RE = {
+    32: {"eq": 24.12, "eq_neq": 24.14, "geq": 24.16, "ext": 24.12, "avg": 24.09},
+    64: {"eq": 25.35, "eq_neq": 25.32, "geq": 25.33, "ext": 25.34, "avg": 25.33},
+    128: {"eq": 25.89, "eq_neq": 25.88, "geq": 25.89, "ext": 25.86, "avg": 25.86},
+}
+
+
+def gas_centroid(sim):
+    """Centre of mass in z of the largest bubble (its gas cells count 1, its
+    interface cells 1 - phi), that bubble's volume, and the number of
+    bubbles."""
+    t = sim.types()
+    phi = sim.phi()
+    lab = sim.bubbles()
+    w = np.where(t == 0, 1.0, np.where(t == 1, 1.0 - phi, 0.0))
+    z = np.broadcast_to((np.arange(t.shape[0]) + 0.5)[:, None, None], t.shape)
+    sel = lab >= 0
+    roots, inv = np.unique(lab[sel], return_inverse=True)
+    vol = np.bincount(inv, weights=w[sel])
+    mom = np.bincount(inv, weights=(w * z)[sel])
+    k = int(np.argmax(vol))
+    return float(mom[k] / vol[k]), float(vol[k]), int(np.unique(lab[t == 0]).size)
+
+
+def taylor_bubble(D: int, scheme: str, precision: str = "fp32", t_samples=(10.0, 15.0),
+                  device: int = 0):
+    """Rise of the Taylor bubble: Re = D u / nu with u the velocity of the
+    largest bubble's centre of mass between the two sample times
+    t* = t sqrt(g / D)."""
+    from . import fsl
+    w = inputs.taylor_bubble(D, refill=scheme)
+    sim = fsl.Sim(w["params"], precision, device=device)
+    sim.init_workload(w)
+    rate = math.sqrt(w["g"] / D)
+    m0 = sim.total_mass()
+    zc0, V0, _ = gas_centroid(sim)
+    samples = []
+    done = 0
+    t0 = time.perf_counter()
+    for ts in t_samples:
+        n = int(round(ts / rate))
+        sim.step(n - done)
+        done = n
+        zc, V, nb = gas_centroid(sim)
+        samples.append(dict(tstar=n * rate, step=n, z=zc, volume=V, bubbles=nb))
+    wall = time.perf_counter() - t0
+    a, b = samples[0], samples[-1]
+    u = (b["z"] - a["z"]) / (b["step"] - a["step"])
+    st = sim.status()
+    lab = sim.bubbles()
+    p = sim.pressure()
+    t = sim.types()
+    pv = p[(t == 1) & (lab >= 0)]
+    out = dict(D=D, scheme=scheme, precision=precision, steps=done, seconds=wall,
+               Re=D * u / w["nu"], paper_Re=PAPER_TAYLOR_RE.get(D, {}).get(scheme),
+               z0=zc0, volume0=V0, samples=samples,
+               bubble_pressure=float(pv.mean()) if pv.size else None,
+               mass_drift=(sim.total_mass() - m0) / m0,
+               unstable_tstar=(st[1] * rate if st[1] >= 0 else None))
+    sim.close()
+    return out
+
+
+def bubbly_poiseuille(scheme: str, precision: str = "fp32", L: int = 100, t_end: float = 4.0,
+                      every: float = 0.5, options=None, device: int = 0):
+    """The bubbly plane Poiseuille flow (Sec. 4.6) to t* = t u_max / L =
+    `t_end`: every `every` in t*, the number of bubbles, the gas fraction,
+    the gas-weighted mean distance |z - L/2| / (L/2) from the channel's
+    centre plane, and max |u| / u_max; the t* of a latched instability.
+    `options` replaces the configuration's option bits (0: no bubble model,
+    every bubble at the constant volume pressure)."""
+    from . import fsl
+    w = inputs.bubbly_poiseuille(L=L, refill=scheme)
+    if options is not None:
+        w["params"]["options"] = options
+    sim = fsl.Sim(w["params"], precision, device=device)
+    sim.init_workload(w)
+    rate = w["u_max"] / L
+    zc = (np.arange(L) + 0.5 - L / 2.0) / (L / 2.0)
+    m0 = sim.total_mass()
+
+    def sample(step):
+        t = sim.types()
+        phi = sim.phi()
+        lab = sim.bubbles()
+        gas = np.where(t == 0, 1.0, np.where(t == 1, 1.0 - phi, 0.0))
+        gz = gas.sum(axis=(1, 2))
+        return dict(tstar=step * rate, bubbles=int(np.unique(lab[t == 0]).size),
+                    gas_fraction=float(gas.sum() / t.size),
+                    centre_distance=float((gz * np.abs(zc)).sum() / gz.sum()),
+                    umax=sim.max_velocity() / w["u_max"])
+
+    samples = [sample(0)]
+    n_every = max(1, int(round(every / rate)))
+    total = int(round(t_end / rate))
+    done = 0
+    t0 = time.perf_counter()
+    while done < total:
+        k = min(n_every, total - done)
+        sim.step(k)
+        done += k
+        samples.append(sample(done))
+        if sim.status()[0] != 0:
+            break
+    wall = time.perf_counter() - t0
+    st = sim.status()
+    out = dict(L=L, scheme=scheme, precision=precision, options=w["params"]["options"],
+               steps=done, seconds=wall, unstable_tstar=(st[1] * rate if st[1] >= 0 else None),
+               mass_drift=(sim.total_mass() - m0) / m0, samples=samples)
+    sim.close()
+    return out
+
+
 def batched_waves(steps: int = 4000, n_geom: int = 64, precision: str = "fp16",
                   chunk: int = 16, tune: bool = True, seed: int = 2207, device: int = 0):
     """The batched standing-wave set: n_geom geometries (wavelength U[32, 256],
@@ -238,11 +361,21 @@ def main():
     ap.add_argument("--save-dir", default=None, help="write each a*(t*) trace as .npy here")
     ap.add_argument("--dam-break", type=int, nargs="*", default=[],
                     help="also run the Sec. 4.2 dam break at these column widths W")
+    ap.add_argument("--taylor", type=int, nargs="*", default=[],
+                    help="also run the Sec. 4.4 Taylor bubble at these tube diameters D")
+    ap.add_argument("--bubbly", action="store_true",
+                    help="also run the Sec. 4.6 bubbly plane Poiseuille flow")
     ap.add_argument("--batched", type=int, default=0,
                     help="also run the batched standing-wave set for this many steps")
     args = ap.parse_args()
     if args.batched:
         print(json.dumps(batched_waves(steps=args.batched)), flush=True)
+    if args.bubbly:
+        for sc in args.schemes:
+            print(json.dumps(bubbly_poiseuille(sc, args.precision)), flush=True)
+    for D in args.taylor:
+        for sc in args.schemes:
+            print(json.dumps(taylor_bubble(D, sc, args.precision)), flush=True)
     for W in args.dam_break:
         for sc in args.schemes:
             print(json.dumps(dam_break(W, sc, args.precision)), flush=True)

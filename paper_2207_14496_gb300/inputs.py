@@ -12,8 +12,9 @@ Geometry conventions (reading R13):
   * walls are a virtual obstacle layer outside the stated domain size.
 
 The workloads restate the paper's experiments in shape (standing gravity wave,
-Sec. 4.1; rectangular dam break, Sec. 4.2; drop impact, Sec. 4.5) at the sizes
-used for parity and measurement.
+Sec. 4.1; rectangular dam break, Sec. 4.2; Taylor bubble, Sec. 4.4; drop
+impact, Sec. 4.5; bubbly plane Poiseuille flow, Sec. 4.6) at the sizes used
+for parity and measurement.
 """
 from __future__ import annotations
 
@@ -220,6 +221,98 @@ def bubbles_in_pool(nx=48, ny=40, depth=32, bubbles=((12.0, 9.0, 4.5), (30.0, 13
                    periodic=(True, False, True), nu=nu, g=(0.0, -g, 0.0), options=16)
     return dict(name=f"bubbles_in_pool_{nx}x{ny}", params=params, phi=phi, u0=None,
                 obstacle=None, h_ref=float(depth))
+
+
+def taylor_bubble(D: int = 32, refill: str = "eq", omega: float = 1.8, mo: float = 0.015,
+                  bo: float = 100.0, collision: str = "srt"):
+    """The paper's Taylor bubble (Sec. 4.4): a tube of diameter D along z
+    (cells whose centre lies more than D/2 from the axis are obstacles) in a
+    D x D x 10D domain, no-slip everywhere, filled with liquid except for a
+    cylindrical gas bubble of diameter 0.75 D and length 3 D whose bottom is
+    D above the floor; D3Q19 SRT at relaxation rate `omega`, gravity -z and
+    surface tension from the Morton number Mo = g mu^4 / (rho sigma^3) and the
+    Bond number Bo = g D^2 / sigma (rho = 1, so mu = nu); hydrostatic density
+    with rho = 1 at z = 5D; the bubble model keeps the bubble's volume
+    pressure, p_V(0) = 1/3."""
+    nu = (1.0 / 3.0) * (1.0 / omega - 0.5)
+    # Mo = nu^4 Bo^3 / (g^2 D^6)  ->  g = nu^2 Bo^1.5 / (sqrt(Mo) D^3)
+    g = nu * nu * bo ** 1.5 / (math.sqrt(mo) * float(D) ** 3)
+    sigma = g * float(D) ** 2 / bo
+    nx = ny = D
+    nz = 10 * D
+    c = D / 2.0
+    J, I = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    outside = (I + 0.5 - c) ** 2 + (J + 0.5 - c) ** 2 > c * c
+    obstacle = np.zeros((nz, ny, nx), dtype=np.uint8)
+    obstacle[:, outside] = 1
+    phi = np.ones((nz, ny, nx))
+    disc = cylinder_fraction(nx, ny, (c, c), 0.375 * D)[0]
+    phi[D:4 * D] = 1.0 - disc
+    phi[:, outside] = 0.0
+    params = _base(q=19, collision=collision, refill=refill, shape=(nx, ny, nz),
+                   periodic=(False, False, False), nu=nu, g=(0.0, 0.0, -g), sigma=sigma,
+                   options=16)
+    return dict(name=f"taylor_bubble_D{D}", params=params, phi=phi, u0=None, obstacle=obstacle,
+                h_ref=5.0 * D, D=D, g=g, sigma=sigma, nu=nu)
+
+
+def bubbly_poiseuille(L: int = 100, n_bubbles: int = 381, refill: str = "eq", seed: int = 2577,
+                      omega: float = 1.989, re: float = 1e4, mo: float = 1e-5,
+                      collision: str = "srt"):
+    """The paper's bubbly plane Poiseuille flow (Sec. 4.6): a 2L x L x L
+    channel, periodic in x and y, no-slip walls in z, driven by a force along
+    x; `n_bubbles` spheres of diameter 0.1 L at seeded random positions (centres
+    at least 0.05 L from the walls, at least one cell of liquid between
+    spheres), gas fraction about 0.1; the liquid starts on the parabola
+    u(z) = F z (L - z) / (2 mu); Re = L u_max / nu with u_max = u(L/2),
+    Mo = F mu^4 / (rho sigma^3) with the driving acceleration in the place of
+    g (rho = 1, so mu = nu); no hydrostatic gradient (the force is along the
+    periodic axis); the bubble model is on."""
+    nu = (1.0 / 3.0) * (1.0 / omega - 0.5)
+    u_max = re * nu / L
+    F = 8.0 * nu * u_max / float(L) ** 2
+    sigma = (F * nu ** 4 / mo) ** (1.0 / 3.0)
+    nx, ny, nz = 2 * L, L, L
+    R = 0.05 * L
+    rng = np.random.default_rng(seed)
+    centres = []
+    tries = 0
+    while len(centres) < n_bubbles:
+        tries += 1
+        if tries > 1000000:
+            raise RuntimeError("could not place the bubbles")
+        c = np.array([rng.uniform(0, nx), rng.uniform(0, ny), rng.uniform(0.05 * L, 0.95 * L)])
+        ok = True
+        for q in centres:
+            d = np.abs(c - q)
+            d[0] = min(d[0], nx - d[0])
+            d[1] = min(d[1], ny - d[1])
+            if float(np.sqrt((d * d).sum())) < 2.0 * R + 2.0:
+                ok = False
+                break
+        if ok:
+            centres.append(c)
+    gas = np.zeros((nz, ny, nx))
+    n = int(math.ceil(2 * R)) + 4
+    for c in centres:
+        o = [int(math.floor(c[a] - R)) - 1 for a in range(3)]
+        loc = sphere_fraction(n, n, n, tuple(c[a] - o[a] for a in range(3)), R)
+        zi = np.arange(o[2], o[2] + n)
+        keep = (zi >= 0) & (zi < nz)
+        yi = np.mod(np.arange(o[1], o[1] + n), ny)
+        xi = np.mod(np.arange(o[0], o[0] + n), nx)
+        gas[np.ix_(zi[keep], yi, xi)] += loc[keep]
+    phi = 1.0 - np.clip(gas, 0.0, 1.0)
+    z = np.arange(nz) + 0.5
+    ux = F / (2.0 * nu) * z * (L - z)
+    u0 = np.zeros((nz, ny, nx, 3))
+    u0[..., 0] = ux[:, None, None]
+    params = _base(q=19, collision=collision, refill=refill, shape=(nx, ny, nz),
+                   periodic=(True, True, False), nu=nu, g=(F, 0.0, 0.0), sigma=sigma,
+                   options=16)
+    return dict(name=f"bubbly_poiseuille_L{L}", params=params, phi=phi, u0=u0, obstacle=None,
+                h_ref=float("nan"), L=L, u_max=u_max, F=F, sigma=sigma, nu=nu,
+                centres=np.array(centres))
 
 
 def static_drop(n=32, radius=8.0, sigma=1e-3, nu=0.1, q=19, two_d=False):

@@ -28,10 +28,14 @@ def _compare_bubbles(sim, orc, label):
     return len(np.unique(lab_o[t == 0]))
 
 
-@pytest.mark.parametrize("case", ["three_bubbles", "merge_then_split"])
+@pytest.mark.parametrize("case", ["three_bubbles", "merge_then_split", "taylor_12"])
 def test_bubbles_parity_fp64(fsl, case):
     if case == "three_bubbles":
         w = inputs.bubbles_in_pool()
+    elif case == "taylor_12":
+        # the Taylor bubble geometry at D = 12: tube of obstacle cells,
+        # gravity along z, hydrostatic start, the tail sheds small bubbles
+        w = inputs.taylor_bubble(12)
     else:
         # two bubbles that merge within 120 steps and break up again
         w = inputs.bubbles_in_pool(nx=36, ny=34, depth=28,

@@ -221,3 +221,30 @@ def test_fixed_point_sums_are_order_free_and_range_checked():
     assert not hi.bubble_range_error()
     hi.bubble_probe(types, phi2, first=False)
     assert hi.bubble_range_error()
+
+
+@pytest.mark.parametrize("D", [16, 32])
+def test_taylor_bubble_setup_matches_paper_numbers(D):
+    """Sec. 4.4 setup: Mo = g nu^4 / sigma^3 = 0.015 and Bo = g D^2 / sigma =
+    100 at relaxation rate 1.8, a bubble of diameter 0.75 D and length 3 D
+    starting D above the floor, in a D x D x 10 D box with a tube of
+    diameter D."""
+    w = inputs.taylor_bubble(D)
+    nu, g, sigma = w["nu"], w["g"], w["sigma"]
+    assert 1.0 / (3.0 * nu + 0.5) == pytest.approx(1.8, rel=1e-14)
+    assert g * nu ** 4 / sigma ** 3 == pytest.approx(0.015, rel=1e-12)
+    assert g * D * D / sigma == pytest.approx(100.0, rel=1e-12)
+    phi, ob = w["phi"], w["obstacle"]
+    assert phi.shape == (10 * D, D, D)
+    open_area = float((ob[0] == 0).sum())
+    assert open_area == pytest.approx(np.pi * D * D / 4, rel=0.05)
+    gas = (1.0 - phi) * (ob == 0)
+    assert gas.sum() == pytest.approx(np.pi * (0.375 * D) ** 2 * 3 * D, rel=1e-3)
+    zs = np.nonzero(gas.sum(axis=(1, 2)))[0]
+    assert zs.min() == D and zs.max() == 4 * D - 1
+    o = oracle.Oracle(w["params"])
+    o.init_fill(phi, obstacle=ob, h_ref=w["h_ref"])
+    lab, p = o.bubbles()
+    t = o.types()
+    assert np.unique(lab[t == GAS]).size == 1
+    assert np.allclose(p[t == IFACE], 1.0 / 3.0, rtol=1e-14)
