@@ -75,10 +75,14 @@ enum {
   FSL_OPT_GEQ_LITERAL_NU = 2u,   /* GEQ prefactor 1/(2 c_s^2 nu) as printed (default 1/(2 c_s^2 omega)) */
   FSL_OPT_NEQ_LITERAL_MEAN = 4u, /* EQ+NEQ: f_i(y) - f_i^eq(rho_bar, u_bar) as printed */
   FSL_OPT_LAPLACE_LITERAL = 8u,  /* p_G = p_V - 2 sigma kappa (default p_G = p_V + sigma K) */
-  FSL_OPT_BUBBLES = 16u          /* bubble model (Sec. 2.2, Eq. nm-fslbm-pressure-volume):
-                                    every face-connected gas region has its own volume
-                                    pressure p_V(0) V(0)/V(t), p V carried through merges
-                                    and splits; p_volume is the initial pressure */
+  FSL_OPT_BUBBLES = 16u,         /* bubble model (Sec. 2.2, Eq. nm-fslbm-pressure-volume):
+                                    every face-connected region of gas and interface cells
+                                    has its own volume pressure p_V(0) V(0)/V(t), p V
+                                    carried through merges and splits; p_volume is the
+                                    initial pressure */
+  FSL_OPT_BUBBLE_GAS_ONLY = 32u  /* with FSL_OPT_BUBBLES: regions of gas cells alone, each
+                                    interface cell attached to the smallest-labelled
+                                    region among its gas stencil neighbours */
 };
 
 typedef struct {

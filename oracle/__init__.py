@@ -35,6 +35,7 @@ OPT_GEQ_LITERAL_NU = 2
 OPT_NEQ_LITERAL_MEAN = 4
 OPT_LAPLACE_LITERAL = 8
 OPT_BUBBLES = 16
+OPT_BUBBLE_GAS_ONLY = 32   # bubbles from gas cells alone, interface cells attached
 
 GAS, IFACE, LIQUID, OBST = 0, 1, 2, 3
 

@@ -75,6 +75,7 @@
 #define ORC_OPT_NEQ_LITERAL_MEAN 4u  /* f^neq = f(y) - f^eq(rho_bar, u_bar) as printed */
 #define ORC_OPT_LAPLACE_LITERAL 8u   /* p_G = p_V - 2 sigma kappa, kappa = -div n_hat */
 #define ORC_OPT_BUBBLES 16u          /* volume pressure per enclosed gas region (bubble model) */
+#define ORC_OPT_BUBBLE_GAS_ONLY 32u  /* bubbles from gas cells alone (interface cells attached) */
 
 #define CLS_STD 0
 #define CLS_NF 1 /* interface cell without liquid neighbour */
@@ -375,11 +376,14 @@ static void update_curvature(orc_state *s) {
 /* Sec. 2.2, Eq. nm-fslbm-pressure-volume: an enclosed gas volume (a bubble)
  * has the volume pressure p_V(t) = p_V(0) V(0) / V(t).  Bubbles merge and
  * split, so (reading R23) the invariant K = p V is carried per bubble:
- *  - bubbles are the connected components of gas cells, connected through
- *    the 6 face neighbours (with periodic wrap); the label of a component
- *    is its smallest cell index;
- *  - an interface cell belongs to the bubble with the smallest label among
- *    its gas stencil neighbours (none: no bubble, no gas PDF to rebuild);
+ *  - bubbles are the connected components of gas and interface cells,
+ *    connected through the 6 face neighbours (with periodic wrap); the
+ *    label of a component is its smallest cell index.  Two bubbles merge
+ *    when their interface layers touch, and a bubble splits only when a
+ *    liquid cell separates its parts;
+ *  - with ORC_OPT_BUBBLE_GAS_ONLY the components are those of gas cells
+ *    alone, and an interface cell belongs to the bubble with the smallest
+ *    label among its gas stencil neighbours (none: no bubble);
  *  - a bubble's volume is sum of w over its cells, w = 1 for gas and
  *    1 - phi for interface cells;
  *  - K of a new component = sum over old bubbles b of K_b times the share
@@ -432,9 +436,12 @@ static int bubble_update(orc_state *s, int first) {
   s->bub_range = 0;
   bub_scales(s);
   for (long x = 0; x < N; ++x) lab[x] = -1;
-  /* components of gas cells: breadth-first from the smallest unlabelled cell */
+  const int gas_only = (s->c.options & ORC_OPT_BUBBLE_GAS_ONLY) != 0;
+  /* members: gas cells, and interface cells unless gas_only */
+#define BUB_MEMBER(t) ((t) == ORC_GAS || (!gas_only && (t) == ORC_IFACE))
+  /* components of members: breadth-first from the smallest unlabelled cell */
   for (long x = 0; x < N; ++x) {
-    if (s->type[x] != ORC_GAS || lab[x] >= 0) continue;
+    if (!BUB_MEMBER(s->type[x]) || lab[x] >= 0) continue;
     long head = 0, tail = 0;
     s->bqueue[tail++] = x;
     lab[x] = x;
@@ -442,15 +449,17 @@ static int bubble_update(orc_state *s, int first) {
       long y = s->bqueue[head++];
       for (int d = 1; d <= 6; ++d) {
         long n = neighbour(s, y, d, 1);
-        if (n >= 0 && s->type[n] == ORC_GAS && lab[n] < 0) {
+        if (n >= 0 && BUB_MEMBER(s->type[n]) && lab[n] < 0) {
           lab[n] = x;
           s->bqueue[tail++] = n;
         }
       }
     }
   }
-  /* interface cells: smallest label among gas stencil neighbours */
-  for (long x = 0; x < N; ++x) {
+#undef BUB_MEMBER
+  /* gas_only: interface cells take the smallest label among gas stencil
+   * neighbours */
+  for (long x = 0; gas_only && x < N; ++x) {
     if (s->type[x] != ORC_IFACE) continue;
     long best = -1;
     for (int d = 1; d < q; ++d) {

@@ -77,6 +77,7 @@ void make_geom(const fsl_config* c, Geom* g) {
   g->variant = FSL_VARIANT_DEFAULT;
   g->free_slip = 0;
   g->bubbles = (c->options & FSL_OPT_BUBBLES) ? 1 : 0;
+  g->bub_gas_only = (c->options & FSL_OPT_BUBBLE_GAS_ONLY) ? 1 : 0;
   for (int a = 0; a < 3; ++a)
     if (c->free_slip[a] && !c->periodic[a]) g->free_slip |= 1 << a;
 }

@@ -2,12 +2,14 @@
 // region has the volume pressure p_V(t) = p_V(0) V(0) / V(t), and regions
 // merge and split.  The invariant K = p V of every bubble is carried from
 // step to step (option FSL_OPT_BUBBLES):
-//   - bubbles are the face-connected components of gas cells (periodic wrap
-//     included), labelled by their smallest cell index: union-find with
-//     atomicMin links (the larger root always points to the smaller one, so
-//     the final root is the component's smallest cell), then flattening;
-//   - an interface cell belongs to the bubble with the smallest label among
-//     its gas stencil neighbours (none: no bubble);
+//   - bubbles are the face-connected components of gas and interface cells
+//     (periodic wrap included), labelled by their smallest cell index:
+//     union-find with atomicMin links (the larger root always points to the
+//     smaller one, so the final root is the component's smallest cell), then
+//     flattening.  Bubbles merge when their interface layers touch;
+//   - with FSL_OPT_BUBBLE_GAS_ONLY the components are those of gas cells
+//     alone, and an interface cell belongs to the bubble with the smallest
+//     label among its gas stencil neighbours (none: no bubble);
 //   - a bubble's volume V is the sum of 1 per gas cell and 1 - phi per
 //     interface cell; its new K is the sum, over the cells it holds that
 //     were in a bubble b before, of K_b times the cell's share of b's volume
@@ -103,13 +105,20 @@ __device__ __forceinline__ long long bub_wq(const Dev& d, int c, double vs, bool
   return __double2ll_rn(w * vs);
 }
 
-// every gas cell its own root; clear the sums of the new roots (gas cells)
-// and the seen volume of the old roots
+// cells that make up the components: gas cells, and interface cells unless
+// the gas-only reading is selected
+__device__ __forceinline__ bool bub_member(const Geom& g, uint8_t fl) {
+  const int t = fl & F_TYPE;
+  return t == T_GAS || (!g.bub_gas_only && t == T_IF);
+}
+
+// every member its own root; clear the sums of the new roots (members) and
+// the seen volume of the old roots
 static __global__ void k_bub_init(Dev d, Geom g, int first) {
   FSL_GRID_LOOP(k, (unsigned)g.cells) {
     const int c = (int)k;
     const int x = c % g.sx;
-    const bool gas = x < g.nx && (d.flags[c] & F_TYPE) == T_GAS;
+    const bool gas = x < g.nx && bub_member(g, d.flags[c]);
     d.bnew[c] = gas ? c : -1;
     if (gas) {
       d.bV[c] = 0;
@@ -126,22 +135,22 @@ static __global__ void k_bub_union(Dev d, Geom g) {
     const int c = (int)k;
     int x, y, z;
     cell_xyz(g, c, x, y, z);
-    if (x >= g.nx || (d.flags[c] & F_TYPE) != T_GAS) continue;
+    if (x >= g.nx || !bub_member(g, d.flags[c])) continue;
     // the three face neighbours below: every face pair (wrap included) once
     const int nbs[3] = {nb_at(g, x, y, z, -1, 0, 0), nb_at(g, x, y, z, 0, -1, 0),
                         nb_at(g, x, y, z, 0, 0, -1)};
     for (int a = 0; a < 3; ++a) {
       const int n = nbs[a];
-      if (n >= 0 && n != c && (d.flags[n] & F_TYPE) == T_GAS)
+      if (n >= 0 && n != c && bub_member(g, d.flags[n]))
         if (!bub_unite(d.bnew, c, n)) atomicOr(&ctrl->timeout, 8u);
     }
   }
 }
 
-// gas cells point straight at their root; an interface cell takes the
-// smallest root among its gas stencil neighbours.  Concurrent finds stay
-// valid: flattening only ever stores a cell's root, and interface cells are
-// on no gas cell's path.
+// members point straight at their root; in the gas-only reading an
+// interface cell takes the smallest root among its gas stencil neighbours.
+// Concurrent finds stay valid: flattening only ever stores a cell's root,
+// and (gas-only) interface cells are on no gas cell's path.
 template <int Q>
 __global__ void k_bub_label(Dev d, Geom g) {
   FSL_GRID_LOOP(k, (unsigned)g.cells) {
@@ -149,8 +158,9 @@ __global__ void k_bub_label(Dev d, Geom g) {
     int x, y, z;
     cell_xyz(g, c, x, y, z);
     if (x >= g.nx) continue;
-    const uint8_t t = d.flags[c] & F_TYPE;
-    if (t == T_GAS) {
+    const uint8_t fl = d.flags[c];
+    const uint8_t t = fl & F_TYPE;
+    if (bub_member(g, fl)) {
       d.bnew[c] = bub_find(d.bnew, c);
     } else if (t == T_IF) {
       int best = -1;

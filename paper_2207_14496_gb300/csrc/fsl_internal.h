@@ -60,6 +60,7 @@ struct Geom {
   int free_slip;       // bit a: the walls of non-periodic axis a are free-slip (specular)
   int variant;         // bulk kernel of the 16/32-bit path (FSL_VARIANT_*; 0 = default)
   int bubbles;         // bubble model on (FSL_OPT_BUBBLES)
+  int bub_gas_only;    // bubbles from gas cells alone (FSL_OPT_BUBBLE_GAS_ONLY)
 };
 
 struct Phys {

@@ -36,6 +36,7 @@ OBS_LOST_MASS, OBS_TRACE = 9, 10
 OBS_FIELD_PDF, OBS_FIELD_TYPES, OBS_FIELD_PHI, OBS_FIELD_MASS, OBS_FIELD_KAPPA = 16, 17, 18, 19, 20
 OBS_FIELD_BUBBLE, OBS_FIELD_PRESSURE = 21, 22
 OPT_BUBBLES = 16
+OPT_BUBBLE_GAS_ONLY = 32
 
 STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "workspace", -4: "unstable",
           -5: "timeout", -6: "state"}

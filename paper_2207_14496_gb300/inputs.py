@@ -262,8 +262,8 @@ def bubbly_poiseuille(L: int = 100, n_bubbles: int = 381, refill: str = "eq", se
     """The paper's bubbly plane Poiseuille flow (Sec. 4.6): a 2L x L x L
     channel, periodic in x and y, no-slip walls in z, driven by a force along
     x; `n_bubbles` spheres of diameter 0.1 L at seeded random positions (centres
-    at least 0.05 L from the walls, at least one cell of liquid between
-    spheres), gas fraction about 0.1; the liquid starts on the parabola
+    at least 0.05 L from the walls, at least three cells between the
+    spheres' surfaces), gas fraction about 0.1; the liquid starts on the parabola
     u(z) = F z (L - z) / (2 mu); Re = L u_max / nu with u_max = u(L/2),
     Mo = F mu^4 / (rho sigma^3) with the driving acceleration in the place of
     g (rho = 1, so mu = nu); no hydrostatic gradient (the force is along the
@@ -287,7 +287,7 @@ def bubbly_poiseuille(L: int = 100, n_bubbles: int = 381, refill: str = "eq", se
             d = np.abs(c - q)
             d[0] = min(d[0], nx - d[0])
             d[1] = min(d[1], ny - d[1])
-            if float(np.sqrt((d * d).sum())) < 2.0 * R + 2.0:
+            if float(np.sqrt((d * d).sum())) < 2.0 * R + 3.0:
                 ok = False
                 break
         if ok:

@@ -3,7 +3,9 @@ p_V(t) = p_V(0) V(0) / V(t) per enclosed gas volume, bubbles merging and
 splitting).  Checked against a library labelling, brute force on small
 grids, and the invariants the bookkeeping must keep: p V per bubble without
 topology change, the sum of p V through a merge, one pressure for the parts
-of a split bubble, and mass conservation with the model on."""
+of a split bubble, and mass conservation with the model on.  Both
+connectivity readings are pinned: gas and interface cells together (the
+default) and gas cells alone with interface cells attached (option 32)."""
 import numpy as np
 import pytest
 
@@ -15,20 +17,24 @@ ndimage = pytest.importorskip("scipy.ndimage")
 GAS, IFACE, LIQ = 0, 1, 2
 
 
-def _orc(shape, periodic=(False, False, False), p_v=1.0 / 3.0, q=19):
+MODES = {"gas_iface": oracle.OPT_BUBBLES,
+         "gas_only": oracle.OPT_BUBBLES | oracle.OPT_BUBBLE_GAS_ONLY}
+
+
+def _orc(shape, periodic=(False, False, False), p_v=1.0 / 3.0, q=19, mode="gas_iface"):
     params = inputs._base(q=q, collision="srt", refill="eq", shape=shape, periodic=periodic,
                           nu=0.05, g=(0.0, 0.0, 0.0))
-    params["options"] = oracle.OPT_BUBBLES
+    params["options"] = MODES[mode]
     params["p_v"] = p_v
     return oracle.Oracle(params)
 
 
-def _blobs(shape, seed):
+def _blobs(shape, seed, frac=0.55):
     """Random gas blobs in liquid with interface cells around them."""
     nx, ny, nz = shape
     rng = np.random.default_rng(seed)
     # 55% before the opening leaves several components of a few cells each
-    gas = rng.random((nz, ny, nx)) < 0.55
+    gas = rng.random((nz, ny, nx)) < frac
     gas = ndimage.binary_opening(gas)
     types = np.full((nz, ny, nx), LIQ, dtype=np.uint8)
     types[gas] = GAS
@@ -39,15 +45,19 @@ def _blobs(shape, seed):
     return types, phi
 
 
+@pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("seed", [1, 2, 3])
-def test_gas_components_match_library_labelling(seed):
-    shape = (14, 11, 9)
-    types, phi = _blobs(shape, seed)
-    o = _orc(shape)
+def test_gas_components_match_library_labelling(seed, mode):
+    # large and sparse enough that the interface layers leave several
+    # gas + interface components
+    shape = (24, 20, 16)
+    types, phi = _blobs(shape, seed, frac=0.45)
+    o = _orc(shape, mode=mode)
     lab, p = o.bubble_probe(types, phi, first=True)
-    ref, n = ndimage.label(types == GAS, structure=ndimage.generate_binary_structure(3, 1))
+    member = (types == GAS) if mode == "gas_only" else (types == GAS) | (types == IFACE)
+    ref, n = ndimage.label(member, structure=ndimage.generate_binary_structure(3, 1))
     assert n >= 3
-    gas = types == GAS
+    gas = member
     # same partition, labels = smallest flat index of the component
     flat = np.arange(types.size).reshape(types.shape)
     for k in range(1, n + 1):
@@ -55,15 +65,17 @@ def test_gas_components_match_library_labelling(seed):
         labels = np.unique(lab[cells])
         assert labels.size == 1
         assert labels[0] == flat[cells].min()
-    assert (lab[~gas & (types != IFACE)] == -1).all()
+    assert (lab[types == LIQ] == -1).all()
     # every bubble starts at the volume pressure
     assert np.allclose(p[gas], 1.0 / 3.0, rtol=0, atol=1e-15)
 
 
 def test_interface_cells_take_smallest_gas_neighbour_label():
+    """Gas-only reading: an interface cell joins the bubble with the smallest
+    label among its gas stencil neighbours."""
     shape = (12, 10, 8)
     types, phi = _blobs(shape, 7)
-    o = _orc(shape, q=27)
+    o = _orc(shape, q=27, mode="gas_only")
     lab, _ = o.bubble_probe(types, phi, first=True)
     nz, ny, nx = types.shape
     for z, y, x in zip(*np.nonzero(types == IFACE)):
@@ -84,7 +96,8 @@ def _volume(types, phi, lab, root):
     return float(np.sum(np.where(types[cells] == GAS, 1.0, 1.0 - phi[cells])))
 
 
-def test_compression_keeps_pv_and_merge_adds_pv():
+@pytest.mark.parametrize("mode", list(MODES))
+def test_compression_keeps_pv_and_merge_adds_pv(mode):
     """Two bubbles, then the first compressed (its interface cells fuller),
     then both joined by a gas bridge."""
     shape = (16, 6, 1)
@@ -97,7 +110,7 @@ def test_compression_keeps_pv_and_merge_adds_pv():
     types[0, 2:4, 10:13] = GAS
     phi[types == IFACE] = 0.5
     phi[types == GAS] = 0.0
-    o = _orc(shape, p_v=0.3)
+    o = _orc(shape, p_v=0.3, mode=mode)
     lab, p = o.bubble_probe(types, phi, first=True)
     ra, rb = lab[0, 2, 2], lab[0, 2, 10]
     assert ra != rb
@@ -128,14 +141,15 @@ def test_compression_keeps_pv_and_merge_adds_pv():
     assert p3[0, 2, 2] * V3 == pytest.approx(Ka + Kb, rel=1e-13)
 
 
-def test_split_bubble_keeps_its_pressure_in_every_part():
+@pytest.mark.parametrize("mode", list(MODES))
+def test_split_bubble_keeps_its_pressure_in_every_part(mode):
     shape = (14, 5, 1)
     nz, ny, nx = 1, 5, 14
     types = np.full((nz, ny, nx), LIQ, dtype=np.uint8)
     types[0, 1:4, 1:13] = IFACE
     types[0, 2, 2:12] = GAS
     phi = np.where(types == IFACE, 0.4, np.where(types == GAS, 0.0, 1.0))
-    o = _orc(shape, p_v=0.25)
+    o = _orc(shape, p_v=0.25, mode=mode)
     lab, p = o.bubble_probe(types, phi, first=True)
     # compress, then cut the bubble in two with a liquid plug
     phi2 = np.where(types == IFACE, 0.7, phi)
@@ -191,7 +205,8 @@ def test_mass_conserved_with_bubbles_through_conversions():
     assert p[gas][0] != 1.0 / 3.0
 
 
-def test_fixed_point_sums_are_order_free_and_range_checked():
+@pytest.mark.parametrize("mode", list(MODES))
+def test_fixed_point_sums_are_order_free_and_range_checked(mode):
     """The volume and K sums are fixed-point integers: relabelling the grid by
     a mirror (which reverses the summation order) gives the same pressures
     bit for bit, and a share of K of 16 or more is flagged."""
@@ -207,16 +222,16 @@ def test_fixed_point_sums_are_order_free_and_range_checked():
     cut = (types == IFACE) & two & (ndimage.maximum_filter(ref, size=3, mode="constant") > 0)
     types[cut] = LIQ
     phi[cut] = 1.0
-    o = _orc(shape)
+    o = _orc(shape, mode=mode)
     o.bubble_probe(types, phi, first=True)
     phi2 = np.where(types == IFACE, np.clip(phi + 0.1, 0, 1), phi)
     _, p = o.bubble_probe(types, phi2, first=False)
-    m = _orc(shape)
+    m = _orc(shape, mode=mode)
     m.bubble_probe(types[::-1, ::-1, ::-1], phi[::-1, ::-1, ::-1], first=True)
     _, pm = m.bubble_probe(types[::-1, ::-1, ::-1], phi2[::-1, ::-1, ::-1], first=False)
     assert np.array_equal(p, pm[::-1, ::-1, ::-1])
     assert not o.bubble_range_error()
-    hi = _orc(shape, p_v=20.0)
+    hi = _orc(shape, p_v=20.0, mode=mode)
     hi.bubble_probe(types, phi, first=True)
     assert not hi.bubble_range_error()
     hi.bubble_probe(types, phi2, first=False)
@@ -248,3 +263,25 @@ def test_taylor_bubble_setup_matches_paper_numbers(D):
     t = o.types()
     assert np.unique(lab[t == GAS]).size == 1
     assert np.allclose(p[t == IFACE], 1.0 / 3.0, rtol=1e-14)
+
+
+def test_touching_interface_layers_merge_and_a_liquid_layer_separates():
+    """Default reading: two bubbles whose interface cells are face
+    neighbours are one bubble; one liquid cell between the interface layers
+    keeps them apart; the gas-only reading keeps them apart in both cases."""
+    def two(gap):
+        nx = 12 + gap
+        types = np.full((1, 5, nx), LIQ, dtype=np.uint8)
+        types[0, 1:4, 1:5] = IFACE
+        types[0, 2, 2:4] = GAS
+        types[0, 1:4, 5 + gap:9 + gap] = IFACE
+        types[0, 2, 6 + gap:8 + gap] = GAS
+        phi = np.where(types == IFACE, 0.5, np.where(types == GAS, 0.0, 1.0))
+        return types, phi
+    for gap, merged in ((0, True), (1, False)):
+        types, phi = two(gap)
+        shape = (types.shape[2], 5, 1)
+        lab, _ = _orc(shape).bubble_probe(types, phi, first=True)
+        assert (lab[0, 2, 2] == lab[0, 2, 6 + gap]) == merged
+        lab, _ = _orc(shape, mode="gas_only").bubble_probe(types, phi, first=True)
+        assert lab[0, 2, 2] != lab[0, 2, 6 + gap]
