@@ -55,6 +55,8 @@ KERNEL_OF = {"pair": "k_stream_collide_lp", "pair_r128": "k_stream_collide_lp",
 # contraction (one FP64 instruction per operation): 152 SMs x 2 FP64 lanes
 # per SM per clock x 2.07 GHz (= 1.26 TFLOP/s when counted as FMA flops).
 FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
+# nominal HBM3e bandwidth of the part, for the second roofline fraction
+NOMINAL_HBM_GBS = 7900.0
 
 
 class ClockSampler:
@@ -304,6 +306,11 @@ def main():
     n_cells = int(np.prod(w["params"]["shape"]))
     value = replica_mlups(n_cells, h["steps"], ms_max, world)
 
+    def fluid_mlups(r):
+        # liquid + interface cells (mean of the counts before and after the
+        # timed steps) per second
+        return (r["n_liquid"] + r["n_interface"]) * r["steps"] / (r["ms"] * 1e-3) / 1e6
+
     def roofline(r, prec):
         if prec == "fp64":
             # FP64 is bound by the FP64 pipe on GB300: algorithmic flops of the
@@ -316,7 +323,8 @@ def main():
                         peak_source="152 SMs x 2 FP64 lanes/clk x 2.07 GHz, one op per instruction")
         ach = r["kernel_bytes"] / (r["kernel_ms"] * 1e-3) / 1e9
         return dict(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
-                    frac=ach / peaks["hbm_gbs"], traffic=TRAFFIC.get((prec, r["variant"])),
+                    frac=ach / peaks["hbm_gbs"], frac_nominal=ach / NOMINAL_HBM_GBS,
+                    traffic=TRAFFIC.get((prec, r["variant"])),
                     kernel=KERNEL_OF.get(r["variant"], "k_stream_collide_lp"),
                     variant=r["variant"], peak_source=peaks["source"])
 
@@ -324,6 +332,7 @@ def main():
     for p in precs:
         r = res[p]
         by_prec[p] = dict(mlups=r["mlups"], ms_per_step=r["ms_per_step"], steps=r["steps"],
+                          fluid_mlups=fluid_mlups(r),
                           kernel_ms=r["kernel_ms"], kernel_bytes=r["kernel_bytes"],
                           roofline=roofline(r, p), status=list(r["status"]),
                           clocks=r["clocks"], variant=r["variant"], tuning_ms=r["tuning_ms"])
@@ -352,6 +361,7 @@ def main():
                         l2="inputs larger than L2 (PDF buffers >= 1.8 GB)"),
             roofline=by_prec[head]["roofline"], cpu_baseline=cpu, e2e=e2e,
             gpu_launches=h["launches"],
+            fluid_mlups=world * by_prec[head]["fluid_mlups"],
             clocks=dict(sm_mhz=clocks["sm_mhz"], sm_max_mhz=clocks["sm_max_mhz"],
                         reasons=clocks["reasons"], samples=clocks["samples"]),
             by_precision=by_prec,
@@ -368,13 +378,11 @@ def main():
 # D3Q27 TRT with Guo forcing (adds, multiplies, divides as written in the
 # kernel source, each shared subexpression counted once).
 FLOPS_PER_CELL_D3Q27_TRT = 1060
-# DRAM bytes per launch of k_stream_collide from the ncu capture summarised
-# under profiles/ (null until captured for the current kernel).
 # DRAM bytes (read + write) per launch of the bulk kernel at 256^3, from one
 # ncu capture per (storage, variant) on the 160^3 case scaled by the
-# launches' algorithmic bytes; None for a
-# kernel without a capture of its current code.
-TRAFFIC = {("fp16", "pair_r96"): 568e6}
+# launches' algorithmic bytes; None for a kernel without a capture of its
+# current code.
+TRAFFIC = {}
 
 if __name__ == "__main__":
     main()
