@@ -378,11 +378,12 @@ def main():
 # D3Q27 TRT with Guo forcing (adds, multiplies, divides as written in the
 # kernel source, each shared subexpression counted once).
 FLOPS_PER_CELL_D3Q27_TRT = 1060
-# DRAM bytes (read + write) per launch of the bulk kernel at 256^3, from one
-# ncu capture per (storage, variant) on the 160^3 case scaled by the
-# launches' algorithmic bytes; None for a kernel without a capture of its
-# current code.
-TRAFFIC = {}
+# DRAM bytes (read + write) per launch of the bulk kernel on the 256^3
+# workload, from one single-pass ncu capture of the autotuner's launches of
+# each variant; None for a kernel without a capture of its current code.
+TRAFFIC = {("fp16", "pair_r128"): 667.0e6, ("fp16", "pair"): 666.8e6,
+           ("fp16", "pair_r96"): 672.7e6, ("fp16", "pair_r80"): 693.9e6,
+           ("fp16", "quad64"): 671.3e6}
 
 if __name__ == "__main__":
     main()
