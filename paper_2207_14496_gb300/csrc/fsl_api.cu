@@ -560,7 +560,8 @@ fsl_status fsl_observe(fsl_handle* h, int what, void* host_out, size_t bytes) {
       // the pressure lives at each bubble's root: expand it per cell into the
       // next-K scratch, which the next step re-initialises anyway
       double* tmp = reinterpret_cast<double*>(h->d.bKnew);
-      k_bub_expand<<<4 * 152, 256, 0, h->stream>>>(h->d, h->g, h->p.p_v, tmp);
+      k_bub_expand<<<(unsigned)((h->g.cells + 255) / 256), 256, 0, h->stream>>>(h->d, h->g,
+                                                                              h->p.p_v, tmp);
       FSL_CK(cudaGetLastError());
       return copy_field(h, tmp, sizeof(double), host_out);
     }

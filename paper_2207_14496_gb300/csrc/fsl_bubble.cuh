@@ -32,7 +32,8 @@
 namespace fsl {
 
 __device__ __forceinline__ int bub_find(const int* L, int x) {
-  // labels only ever decrease towards the root, so the walk ends
+  // labels only ever decrease towards the root, so the walk ends (path
+  // halving with atomicMin was measured slower: the hot ancestors contend)
   int r = L[x];
   while (r != x) {
     x = r;
@@ -252,7 +253,10 @@ static __global__ void k_bub_expand(Dev d, Geom g, double p_v, double* out) {
 // the whole update (first: bubbles of the initial state, K = p_V V)
 template <int Q>
 cudaError_t bubble_update(const Dev& d, const Geom& g, const Phys& p, int first, cudaStream_t s) {
-  const int blocks = 4 * 152;
+  // one thread per cell: these passes do one or two dependent memory round
+  // trips per cell, so as many cells as possible should be in flight (a
+  // grid-stride loop over a small grid would serialise the round trips)
+  const unsigned blocks = (unsigned)((g.cells + 255) / 256);
   const BubScale sc = bub_scale(g);
   k_bub_init<<<blocks, 256, 0, s>>>(d, g, first);
   k_bub_union<<<blocks, 256, 0, s>>>(d, g);
