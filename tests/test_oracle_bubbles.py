@@ -285,3 +285,54 @@ def test_touching_interface_layers_merge_and_a_liquid_layer_separates():
         assert (lab[0, 2, 2] == lab[0, 2, 6 + gap]) == merged
         lab, _ = _orc(shape, mode="gas_only").bubble_probe(types, phi, first=True)
         assert lab[0, 2, 2] != lab[0, 2, 6 + gap]
+
+
+def test_bubbly_poiseuille_setup_matches_paper_numbers():
+    """Sec. 4.6 setup: 2L x L x L, 381 spheres of diameter 0.1 L, gas
+    fraction about 0.1, centres at least 0.05 L from the walls, Re = 1e4 and
+    Mo = 1e-5 at relaxation rate 1.989, the liquid on the Poiseuille
+    parabola with its maximum u_max at mid-channel."""
+    w = inputs.bubbly_poiseuille()
+    L, nu, F, sigma = w["L"], w["nu"], w["F"], w["sigma"]
+    assert 1.0 / (3.0 * nu + 0.5) == pytest.approx(1.989, rel=1e-14)
+    assert L * w["u_max"] / nu == pytest.approx(1e4, rel=1e-12)
+    assert F * nu ** 4 / sigma ** 3 == pytest.approx(1e-5, rel=1e-12)
+    assert w["phi"].shape == (L, L, 2 * L)
+    assert 1.0 - w["phi"].mean() == pytest.approx(0.1, abs=0.005)
+    c = w["centres"]
+    assert len(c) == 381
+    assert c[:, 2].min() >= 0.05 * L and c[:, 2].max() <= 0.95 * L
+    d = np.abs(c[:, None, :] - c[None, :, :])
+    d[..., 0] = np.minimum(d[..., 0], 2 * L - d[..., 0])
+    d[..., 1] = np.minimum(d[..., 1], L - d[..., 1])
+    r = np.sqrt((d * d).sum(axis=-1)) + np.eye(len(c)) * 1e9
+    assert r.min() >= 0.1 * L + 3.0
+    ux = w["u0"][:, 0, 0, 0]
+    assert ux.max() == pytest.approx(w["u_max"], rel=1e-3)
+    assert ux[0] == pytest.approx(ux[-1], rel=1e-12)
+
+
+def test_largest_bubble_centroid_of_the_taylor_start():
+    """The experiments' centre of mass of the largest bubble, on the initial
+    Taylor-bubble state: the bubble spans z in [D, 4D), so its centre is at
+    z = 2.5 D, and its volume is the gas volume of the setup."""
+    from paper_2207_14496_gb300 import experiments
+    w = inputs.taylor_bubble(12)
+    o = oracle.Oracle(w["params"])
+    o.init_fill(w["phi"], obstacle=w["obstacle"], h_ref=w["h_ref"])
+
+    class View:
+        def types(self):
+            return o.types()
+
+        def phi(self):
+            return o.phi()
+
+        def bubbles(self):
+            return o.bubbles()[0]
+
+    z, V, n = experiments.gas_centroid(View())
+    gas = ((1.0 - w["phi"]) * (w["obstacle"] == 0)).sum()
+    assert z == pytest.approx(2.5 * 12, rel=1e-12)
+    assert V == pytest.approx(gas, rel=1e-12)
+    assert n == 1
