@@ -2152,10 +2152,13 @@ struct Kernels {
     }
     return cudaGetLastError();
   }
+  // kernels of one step: interface pass, bulk pass (plus the tile list of
+  // the TMA variants), fill, empty, finalise, refill, excess share, excess
+  // gather, classify, end of step; six more with the bubble model
   static int launches(const Geom& g) {
     const int bub = g.bubbles ? 6 : 0;
-    if constexpr (ST::kShift) return ((variant_of(g) == 4 || variant_of(g) == 6) ? 12 : 11) + bub;
-    return 11 + bub;
+    if constexpr (ST::kShift) return ((variant_of(g) == 4 || variant_of(g) == 6) ? 11 : 10) + bub;
+    return 10 + bub;
   }
   static const Launch* table() {
     static const Launch L = {&step, &init, &total_mass, &max_velocity, &export_pdf,
