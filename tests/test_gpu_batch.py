@@ -73,3 +73,35 @@ def test_batch_interleaved_with_member_work_and_reinit(fsl):
         _same(_state(r), _state(sims[i]), f"member {i}")
         r.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_batch_with_bubble_model_matches_individual_runs(fsl, prec):
+    """Members with the bubble model (both connectivity readings) beside a
+    member without it: bubble labels and pressures equal the solo runs bit
+    for bit."""
+    ws = [inputs.bubbles_in_pool(), inputs.bubbles_in_pool(nx=36, ny=34, depth=28,
+                                                          bubbles=((14.0, 9.0, 5.0), (26.0, 9.0, 5.0)),
+                                                          g=4e-4),
+          _members()[0]]
+    ws[1]["params"]["options"] = 48
+    solo = []
+    for w in ws:
+        s = fsl.Sim(w["params"], prec)
+        s.init_workload(w)
+        s.step(90)
+        solo.append(_state(s) + (s.bubbles(), s.pressure()))
+        s.close()
+    sims = []
+    for w in ws:
+        s = fsl.Sim(w["params"], prec)
+        s.init_workload(w)
+        sims.append(s)
+    b = fsl.Batch(sims, chunk=16)
+    b.step(90)
+    for i, s in enumerate(sims):
+        st = _state(s) + (s.bubbles(), s.pressure())
+        _same(solo[i][:5], st[:5], f"member {i}")
+        assert np.array_equal(solo[i][5], st[5]), f"member {i}: bubble labels differ"
+        assert np.array_equal(solo[i][6], st[6]), f"member {i}: pressures differ"
+    b.close()
