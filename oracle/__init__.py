@@ -8,10 +8,12 @@ dictionaries plus seeded initial fill levels from the input generators.
 Parity pinned by the ``-m "not gpu"`` tests (lattice moments, Guo moments,
 mass conservation, resting pool, standing-wave frequency and damping,
 Young-Laplace jump, TRT Poiseuille, hand-built refilling neighbourhoods,
-normal/curvature exactness).  Parity unpinned (pinned only by oracle = GPU):
-the Thuerey flux table (R5), excess-mass receivers (R3), conflict priority
-(R6), neighbour means (R7), obstacle narrowing of normals (R11), geometry
-conventions and observables.
+normal/curvature exactness, free-slip plug flow, Smagorinsky closure, one
+periodic layer = D2Q9, and the bubble model: library labelling, p V through
+compression, merge and split, order-free fixed-point sums).  Parity unpinned
+(pinned only by oracle = GPU): the Thuerey flux table (R5), excess-mass
+receivers (R3), conflict priority (R6), neighbour means (R7), obstacle
+narrowing of normals (R11), geometry conventions and observables.
 """
 from __future__ import annotations
 

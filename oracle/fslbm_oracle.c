@@ -27,6 +27,9 @@
  *             free-surface boundary condition (Eq. nm-fslbm-boundary-condition),
  *             gas and Laplace pressure (Eqs. nm-fslbm-pressure-gas, -laplace),
  *             curvature kappa = -div(n_hat), Parker-Youngs normal.
+ *             With the bubble model (option 16): volume pressure per enclosed
+ *             gas region (Eq. nm-fslbm-pressure-volume), regions merging and
+ *             splitting.
  *   Sec. 3.1  refilling: EQ, EQ+NEQ, GEQ, EXT, AVG.
  *   Sec. 3.2  mass neutrality of refilling (Eq. rs-mass-change).
  *
@@ -54,6 +57,10 @@
  *       central two-point difference over non-obstacle cells.
  *   R12 hydrostatic initial density, linear: rho = 1 + 3 g_a (x_a - h_ref).
  *   R16 plain IEEE round-to-nearest FP64, no contraction.
+ *   R23 bubbles: face-connected regions of gas and interface cells (option
+ *       32: gas cells alone, interface cells attached), K = p V carried
+ *       through merges (added) and splits (shared by volume), sums in fixed
+ *       point (see bubble_update).
  */
 #include <math.h>
 #include <stdlib.h>
