@@ -17,11 +17,14 @@
  *   3. refilling of gas->interface cells (Sec. 3.1: EQ, EQ+NEQ, GEQ, EXT, AVG);
  *   4. excess-mass redistribution (Eq. nm-fslbm-excess-mass);
  *   5. Parker-Youngs normals and curvature kappa = -div(n_hat) (Sec. 2.2) for
- *      the Laplace pressure (Eqs. nm-fslbm-pressure-gas, nm-fslbm-pressure-laplace).
+ *      the Laplace pressure (Eqs. nm-fslbm-pressure-gas, nm-fslbm-pressure-laplace);
+ *   6. with FSL_OPT_BUBBLES, the volume pressure of every enclosed gas region
+ *      (Eq. nm-fslbm-pressure-volume), carried through merges and splits.
  *
  * Conventions for every entry point
  *   - Status: 0 on success, a negative fsl_status on failure.  No entry point
- *     aborts or traps; device-side conditions (instability) are latched in a
+ *     aborts or traps; device-side conditions (instability, a bubble sum
+ *     term out of range, a bounded device loop that gave up) are latched in a
  *     device status word and reported by fsl_observe(FSL_OBS_STATUS).
  *   - Memory: the caller owns the device workspace (one allocation of
  *     fsl_workspace_bytes bytes, 256-byte aligned) and the CUDA stream.  The
