@@ -5,8 +5,10 @@
 //   - bubbles are the face-connected components of gas and interface cells
 //     (periodic wrap included), labelled by their smallest cell index:
 //     union-find with atomicMin links (the larger root always points to the
-//     smaller one, so the final root is the component's smallest cell), then
-//     flattening.  Bubbles merge when their interface layers touch;
+//     smaller one, so the final root is the component's smallest cell),
+//     started from runs of members along x and linked once per overlapping
+//     stretch, then flattening.  Bubbles merge when their interface layers
+//     touch;
 //   - with FSL_OPT_BUBBLE_GAS_ONLY the components are those of gas cells
 //     alone, and an interface cell belongs to the bubble with the smallest
 //     label among its gas stencil neighbours (none: no bubble);
@@ -16,7 +18,8 @@
 //     still in bubbles; a bubble with no such cell starts at K = p_V V;
 //   - interface cells see the volume pressure K / V of their bubble, kept
 //     at the bubble's root cell (bp) and read through the cell's label.
-// The sums are fixed-point integers, so their value does not depend on the
+// The sums are fixed-point integers, summed per key in each warp and block
+// before one atomic per key and block, so their value does not depend on the
 // order in which the atomics land: with 2^b the smallest power of two not
 // below nx*ny*nz, a cell's volume term w counts as round(w 2^vshift) units,
 // vshift = 62 - b, and a share of K as round(share 2^kshift) units,
@@ -61,24 +64,63 @@ __device__ __forceinline__ bool bub_unite(int* L, int a, int b) {
   return false;
 }
 
-// sum of v over the lanes of the warp that share key; the lowest such lane
-// adds the sum to *dst (integer: exact in any order)
-__device__ __forceinline__ void warp_keyed_add(bool on, long long key, long long v,
-                                               long long* dst) {
-  const unsigned act = __ballot_sync(0xffffffffu, on);
-  if (!on) return;
-  const unsigned grp = __match_any_sync(act, key);
+// Sum of v over the threads of the block whose keys are equal, added to
+// arr[idx] (idx is the same for equal keys) with one atomic per distinct key
+// per block: lanes with equal keys are summed in their warp, the warps'
+// partial sums are listed in shared memory and summed per key again.  The
+// sums are integers, so the result does not depend on the grouping.  If
+// flag is non-null, the final adder also sets flag[idx] = 1.  Every thread of
+// the block calls it (it synchronises the block); kBubThreads threads.
+constexpr int kBubThreads = 256;
+struct BubSlots {
+  long long key[kBubThreads];
+  long long sum[kBubThreads];
+  int idx[kBubThreads];
+  int n;
+};
+
+__device__ __forceinline__ void block_keyed_add(bool on, long long key, long long v, int idx,
+                                                long long* arr, uint8_t* flag, BubSlots& sh) {
+  const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(grp) - 1;
-  unsigned long long sum = 0;
-  unsigned m = grp;
-  while (m) {
-    const int l = __ffs(m) - 1;
-    const long long t = __shfl_sync(grp, v, l);
-    if (lane == leader) sum += (unsigned long long)t;
-    m &= m - 1;
+  if (threadIdx.x == 0) sh.n = 0;
+  __syncthreads();
+  const unsigned act = __ballot_sync(FULL, on);
+  if (on) {
+    const unsigned grp = __match_any_sync(act, key);
+    const int leader = __ffs(grp) - 1;
+    unsigned long long sum = 0;
+    for (unsigned m = grp; m; m &= m - 1) {
+      const long long t = __shfl_sync(grp, v, __ffs(m) - 1);
+      if (lane == leader) sum += (unsigned long long)t;
+    }
+    if (lane == leader) {
+      const int slot = atomicAdd(&sh.n, 1);
+      sh.key[slot] = key;
+      sh.sum[slot] = (long long)sum;
+      sh.idx[slot] = idx;
+    }
   }
-  if (lane == leader) atomicAdd(reinterpret_cast<unsigned long long*>(dst), sum);
+  __syncthreads();
+  const int j = threadIdx.x;  // warp w sums entries 32 w .. 32 w + 31
+  const bool has = j < sh.n;
+  const unsigned act2 = __ballot_sync(FULL, has);
+  if (has) {
+    const long long k2 = sh.key[j];
+    const long long v2 = sh.sum[j];
+    const unsigned grp = __match_any_sync(act2, k2);
+    const int leader = __ffs(grp) - 1;
+    unsigned long long sum = 0;
+    for (unsigned m = grp; m; m &= m - 1) {
+      const long long t = __shfl_sync(grp, v2, __ffs(m) - 1);
+      if (lane == leader) sum += (unsigned long long)t;
+    }
+    if (lane == leader) {
+      atomicAdd(reinterpret_cast<unsigned long long*>(arr + sh.idx[j]), sum);
+      if (flag) flag[sh.idx[j]] = 1;
+    }
+  }
+  __syncthreads();
 }
 
 // fixed-point scales of the bubble sums
@@ -113,39 +155,68 @@ __device__ __forceinline__ bool bub_member(const Geom& g, uint8_t fl) {
   return t == T_GAS || (!g.bub_gas_only && t == T_IF);
 }
 
-// every member its own root; clear the sums of the new roots (members) and
-// the seen volume of the old roots
+// Union-find start: every member points at the first cell of its run of
+// members within its warp (a warp's 32 cells lie in one row, rows being
+// multiples of 64 cells), so a run is one tree before any union; the sums
+// of the new roots (members) and the seen volume of the old roots are
+// cleared.  One cell per thread, no early exit (warp ballots).
 static __global__ void k_bub_init(Dev d, Geom g, int first) {
-  FSL_GRID_LOOP(k, (unsigned)g.cells) {
-    const int c = (int)k;
-    const int x = c % g.sx;
-    const bool gas = x < g.nx && bub_member(g, d.flags[c]);
-    d.bnew[c] = gas ? c : -1;
-    if (gas) {
-      d.bV[c] = 0;
-      d.bKnew[c] = 0;
-      d.bhas[c] = 0;
-    }
-    if (!first && d.blab[c] == c) d.bVseen[c] = 0;
+  const unsigned FULL = 0xffffffffu;
+  const unsigned k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = k < (unsigned)g.cells;
+  const int c = ok ? (int)k : 0;
+  const int lane = threadIdx.x & 31;
+  const bool mem = ok && c % g.sx < g.nx && bub_member(g, d.flags[c]);
+  const unsigned mm = __ballot_sync(FULL, mem);
+  const unsigned below = ~mm & ((1u << lane) - 1u);  // non-members left of this lane
+  const int start = below ? 32 - __clz(below) : 0;
+  if (!ok) return;
+  d.bnew[c] = mem ? c - lane + start : -1;
+  if (mem) {
+    d.bV[c] = 0;
+    d.bKnew[c] = 0;
+    d.bhas[c] = 0;
   }
+  if (!first && d.blab[c] == c) d.bVseen[c] = 0;
 }
 
+// Links across runs: the first cell of a run links to its member neighbour
+// at x - 1 (the run before it, or the wrap); for the neighbours at y - 1 and
+// z - 1, the first cell of every stretch of the run that lies on members
+// links (its left neighbour's neighbour is not a member, or it starts the
+// run): along a stretch the cells below form one run of the warp below,
+// which already shares one root.  Every face-adjacent pair of members ends
+// up in one tree.
 static __global__ void k_bub_union(Dev d, Geom g) {
+  const unsigned FULL = 0xffffffffu;
   Ctrl* ctrl = d.ctrl;
-  FSL_GRID_LOOP(k, (unsigned)g.cells) {
-    const int c = (int)k;
-    int x, y, z;
-    cell_xyz(g, c, x, y, z);
-    if (x >= g.nx || !bub_member(g, d.flags[c])) continue;
-    // the three face neighbours below: every face pair (wrap included) once
-    const int nbs[3] = {nb_at(g, x, y, z, -1, 0, 0), nb_at(g, x, y, z, 0, -1, 0),
-                        nb_at(g, x, y, z, 0, 0, -1)};
-    for (int a = 0; a < 3; ++a) {
-      const int n = nbs[a];
-      if (n >= 0 && n != c && bub_member(g, d.flags[n]))
-        if (!bub_unite(d.bnew, c, n)) atomicOr(&ctrl->timeout, 8u);
-    }
+  const unsigned k = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool ok = k < (unsigned)g.cells;
+  const int c = ok ? (int)k : 0;
+  const int lane = threadIdx.x & 31;
+  const bool mem = ok && c % g.sx < g.nx && bub_member(g, d.flags[c]);
+  const unsigned mm = __ballot_sync(FULL, mem);
+  if (!mem) return;
+  const bool run_start = lane == 0 || !((mm >> (lane - 1)) & 1u);
+  int x, y, z;
+  cell_xyz(g, c, x, y, z);
+  bool fail = false;
+  if (run_start) {
+    const int n = nb_at(g, x, y, z, -1, 0, 0);
+    if (n >= 0 && n != c && bub_member(g, d.flags[n])) fail |= !bub_unite(d.bnew, c, n);
   }
+  for (int a = 1; a <= 2; ++a) {
+    const int dy = a == 1 ? -1 : 0, dz = a == 2 ? -1 : 0;
+    const int n = nb_at(g, x, y, z, 0, dy, dz);
+    if (n < 0 || n == c || !bub_member(g, d.flags[n])) continue;
+    bool need = run_start;
+    if (!need) {
+      const int nl = nb_at(g, x - 1, y, z, 0, dy, dz);
+      need = !(nl >= 0 && bub_member(g, d.flags[nl]));
+    }
+    if (need) fail |= !bub_unite(d.bnew, c, n);
+  }
+  if (fail) atomicOr(&ctrl->timeout, 8u);
 }
 
 // members point straight at their root; in the gas-only reading an
@@ -184,45 +255,52 @@ __device__ __forceinline__ void bub_flag(const Dev& d, bool bad, int first) {
 }
 
 // volume of every new bubble; volume of every old bubble still in bubbles
-static __global__ void k_bub_volume(Dev d, Geom g, int first, double vs) {
-  FSL_WARP_LOOP(k, ok, (unsigned)g.cells) {
-    const int c = ok ? (int)k : 0;
-    const int r = ok ? d.bnew[c] : -1;
-    const int b = (ok && !first) ? d.blab[c] : -1;
-    bool bad = false;
-    const long long wq = r >= 0 ? bub_wq(d, c, vs, bad) : 0;
-    warp_keyed_add(r >= 0, r, wq, d.bV + (r >= 0 ? r : 0));
-    warp_keyed_add(r >= 0 && b >= 0, b, wq, d.bVseen + (b >= 0 ? b : 0));
-    bub_flag(d, bad, first);
-  }
+// (one cell per thread, kBubThreads threads per block, no early exit: the
+// sums synchronise the block)
+static __global__ void __launch_bounds__(kBubThreads) k_bub_volume(Dev d, Geom g, int first,
+                                                                   double vs) {
+  __shared__ BubSlots sh;
+  const unsigned k = blockIdx.x * kBubThreads + threadIdx.x;
+  const bool ok = k < (unsigned)g.cells;
+  const int c = ok ? (int)k : 0;
+  const int r = ok ? d.bnew[c] : -1;
+  const int b = (ok && !first) ? d.blab[c] : -1;
+  bool bad = false;
+  const long long wq = r >= 0 ? bub_wq(d, c, vs, bad) : 0;
+  block_keyed_add(r >= 0, r, wq, r, d.bV, nullptr, sh);
+  block_keyed_add(r >= 0 && b >= 0, b, wq, b, d.bVseen, nullptr, sh);
+  bub_flag(d, bad, first);
 }
 
 // K of every new bubble from the old bubbles its cells came from
-static __global__ void k_bub_kmap(Dev d, Geom g, double vs, double ks) {
-  FSL_WARP_LOOP(k, ok, (unsigned)g.cells) {
-    const int c = ok ? (int)k : 0;
-    const int r = ok ? d.bnew[c] : -1;
-    const int b = ok ? d.blab[c] : -1;
-    bool on = r >= 0 && b >= 0;
-    bool bad = false;
-    long long v = 0;
+static __global__ void __launch_bounds__(kBubThreads) k_bub_kmap(Dev d, Geom g, double vs,
+                                                                 double ks) {
+  __shared__ BubSlots sh;
+  const unsigned k = blockIdx.x * kBubThreads + threadIdx.x;
+  const bool ok = k < (unsigned)g.cells;
+  const int c = ok ? (int)k : 0;
+  const int r = ok ? d.bnew[c] : -1;
+  const int b = ok ? d.blab[c] : -1;
+  bool on = r >= 0 && b >= 0;
+  bool bad = false;
+  long long v = 0;
+  if (on) {
+    const long long vseen = d.bVseen[b];
+    on = vseen != 0;
     if (on) {
-      const long long vseen = d.bVseen[b];
-      on = vseen != 0;
-      if (on) {
-        const long long wq = bub_wq(d, c, vs, bad);
-        const double share = d.bK[b] * ((double)wq / (double)vseen);
-        if (fabs(share) < 16.0)
-          v = __double2ll_rn(share * ks);
-        else
-          bad = true;
-        d.bhas[r] = 1;
-      }
+      const long long wq = bub_wq(d, c, vs, bad);
+      const double share = d.bK[b] * ((double)wq / (double)vseen);
+      if (fabs(share) < 16.0)
+        v = __double2ll_rn(share * ks);
+      else
+        bad = true;
     }
-    const long long key = on ? ((long long)r << 32) | (unsigned)b : 0;
-    warp_keyed_add(on, key, v, d.bKnew + (on ? r : 0));
-    bub_flag(d, bad, 0);
   }
+  // bubble r receives a share (bhas[r] = 1) whenever one of its cells came
+  // from an old bubble still in bubbles
+  const long long key = on ? ((long long)r << 32) | (unsigned)b : 0;
+  block_keyed_add(on, key, v, on ? r : 0, d.bKnew, d.bhas, sh);
+  bub_flag(d, bad, 0);
 }
 
 // the new labels become the state; K and volume pressure of every bubble at
@@ -261,8 +339,8 @@ cudaError_t bubble_update(const Dev& d, const Geom& g, const Phys& p, int first,
   k_bub_init<<<blocks, 256, 0, s>>>(d, g, first);
   k_bub_union<<<blocks, 256, 0, s>>>(d, g);
   k_bub_label<Q><<<blocks, 256, 0, s>>>(d, g);
-  k_bub_volume<<<blocks, 256, 0, s>>>(d, g, first, sc.vs);
-  if (!first) k_bub_kmap<<<blocks, 256, 0, s>>>(d, g, sc.vs, sc.ks);
+  k_bub_volume<<<blocks, kBubThreads, 0, s>>>(d, g, first, sc.vs);
+  if (!first) k_bub_kmap<<<blocks, kBubThreads, 0, s>>>(d, g, sc.vs, sc.ks);
   k_bub_commit<<<blocks, 256, 0, s>>>(d, g, p.p_v, sc.vinv, sc.kinv);
   return cudaGetLastError();
 }
