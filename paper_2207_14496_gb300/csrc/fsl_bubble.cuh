@@ -254,52 +254,87 @@ __device__ __forceinline__ void bub_flag(const Dev& d, bool bad, int first) {
     atomicCAS(&d.ctrl->unstable_step, -1, d.ctrl->step + 1);
 }
 
+// Cells per thread of the two summing passes: a warp takes 32 kBubCells
+// consecutive cells (lane, lane + 32, ...), and a thread adds the terms of
+// its cells that share the first key it meets in registers (inside a bubble
+// that is all of them) and adds the others straight to their bubble.
+constexpr int kBubCells = 8;
+
+__device__ __forceinline__ long long bub_cell(int j) {
+  const long long w = (long long)blockIdx.x * (kBubThreads / 32) + (threadIdx.x >> 5);
+  return w * (32 * kBubCells) + 32 * j + (threadIdx.x & 31);
+}
+
 // volume of every new bubble; volume of every old bubble still in bubbles
-// (one cell per thread, kBubThreads threads per block, no early exit: the
-// sums synchronise the block)
+// (no early exit: the sums synchronise the block)
 static __global__ void __launch_bounds__(kBubThreads) k_bub_volume(Dev d, Geom g, int first,
                                                                    double vs) {
   __shared__ BubSlots sh;
-  const unsigned k = blockIdx.x * kBubThreads + threadIdx.x;
-  const bool ok = k < (unsigned)g.cells;
-  const int c = ok ? (int)k : 0;
-  const int r = ok ? d.bnew[c] : -1;
-  const int b = (ok && !first) ? d.blab[c] : -1;
+  int r0 = -1, b0 = -1;
+  long long acc_v = 0, acc_s = 0;
   bool bad = false;
-  const long long wq = r >= 0 ? bub_wq(d, c, vs, bad) : 0;
-  block_keyed_add(r >= 0, r, wq, r, d.bV, nullptr, sh);
-  block_keyed_add(r >= 0 && b >= 0, b, wq, b, d.bVseen, nullptr, sh);
+  for (int j = 0; j < kBubCells; ++j) {
+    const long long c = bub_cell(j);
+    if (c >= g.cells) break;
+    const int r = d.bnew[c];
+    if (r < 0) continue;
+    const int b = first ? -1 : d.blab[c];
+    const long long wq = bub_wq(d, (int)c, vs, bad);
+    if (r0 < 0) r0 = r;
+    if (r == r0)
+      acc_v += wq;
+    else
+      atomicAdd(reinterpret_cast<unsigned long long*>(d.bV + r), (unsigned long long)wq);
+    if (b < 0) continue;
+    if (b0 < 0) b0 = b;
+    if (b == b0)
+      acc_s += wq;
+    else
+      atomicAdd(reinterpret_cast<unsigned long long*>(d.bVseen + b), (unsigned long long)wq);
+  }
+  block_keyed_add(r0 >= 0, r0, acc_v, r0, d.bV, nullptr, sh);
+  block_keyed_add(b0 >= 0, b0, acc_s, b0, d.bVseen, nullptr, sh);
   bub_flag(d, bad, first);
 }
 
-// K of every new bubble from the old bubbles its cells came from
+// K of every new bubble from the old bubbles its cells came from; bubble r
+// receives a share (bhas[r] = 1) whenever one of its cells came from an old
+// bubble still in bubbles
 static __global__ void __launch_bounds__(kBubThreads) k_bub_kmap(Dev d, Geom g, double vs,
                                                                  double ks) {
   __shared__ BubSlots sh;
-  const unsigned k = blockIdx.x * kBubThreads + threadIdx.x;
-  const bool ok = k < (unsigned)g.cells;
-  const int c = ok ? (int)k : 0;
-  const int r = ok ? d.bnew[c] : -1;
-  const int b = ok ? d.blab[c] : -1;
-  bool on = r >= 0 && b >= 0;
+  long long key0 = -1;
+  int r0 = 0;
+  long long acc = 0;
   bool bad = false;
-  long long v = 0;
-  if (on) {
+  for (int j = 0; j < kBubCells; ++j) {
+    const long long c = bub_cell(j);
+    if (c >= g.cells) break;
+    const int r = d.bnew[c];
+    const int b = d.blab[c];
+    if (r < 0 || b < 0) continue;
     const long long vseen = d.bVseen[b];
-    on = vseen != 0;
-    if (on) {
-      const long long wq = bub_wq(d, c, vs, bad);
-      const double share = d.bK[b] * ((double)wq / (double)vseen);
-      if (fabs(share) < 16.0)
-        v = __double2ll_rn(share * ks);
-      else
-        bad = true;
+    if (vseen == 0) continue;
+    const long long wq = bub_wq(d, (int)c, vs, bad);
+    const double share = d.bK[b] * ((double)wq / (double)vseen);
+    long long v = 0;
+    if (fabs(share) < 16.0)
+      v = __double2ll_rn(share * ks);
+    else
+      bad = true;
+    const long long key = ((long long)r << 32) | (unsigned)b;
+    if (key0 < 0) {
+      key0 = key;
+      r0 = r;
+    }
+    if (key == key0) {
+      acc += v;
+    } else {
+      atomicAdd(reinterpret_cast<unsigned long long*>(d.bKnew + r), (unsigned long long)v);
+      d.bhas[r] = 1;
     }
   }
-  // bubble r receives a share (bhas[r] = 1) whenever one of its cells came
-  // from an old bubble still in bubbles
-  const long long key = on ? ((long long)r << 32) | (unsigned)b : 0;
-  block_keyed_add(on, key, v, on ? r : 0, d.bKnew, d.bhas, sh);
+  block_keyed_add(key0 >= 0, key0, acc, r0, d.bKnew, d.bhas, sh);
   bub_flag(d, bad, 0);
 }
 
@@ -339,8 +374,10 @@ cudaError_t bubble_update(const Dev& d, const Geom& g, const Phys& p, int first,
   k_bub_init<<<blocks, 256, 0, s>>>(d, g, first);
   k_bub_union<<<blocks, 256, 0, s>>>(d, g);
   k_bub_label<Q><<<blocks, 256, 0, s>>>(d, g);
-  k_bub_volume<<<blocks, kBubThreads, 0, s>>>(d, g, first, sc.vs);
-  if (!first) k_bub_kmap<<<blocks, kBubThreads, 0, s>>>(d, g, sc.vs, sc.ks);
+  const unsigned sum_blocks = (unsigned)((g.cells + kBubThreads * kBubCells - 1) /
+                                         (kBubThreads * kBubCells));
+  k_bub_volume<<<sum_blocks, kBubThreads, 0, s>>>(d, g, first, sc.vs);
+  if (!first) k_bub_kmap<<<sum_blocks, kBubThreads, 0, s>>>(d, g, sc.vs, sc.ks);
   k_bub_commit<<<blocks, 256, 0, s>>>(d, g, p.p_v, sc.vinv, sc.kinv);
   return cudaGetLastError();
 }
