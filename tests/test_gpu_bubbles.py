@@ -34,10 +34,13 @@ MODES = {"gas_iface": 16, "gas_only": 48}
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-@pytest.mark.parametrize("case", ["three_bubbles", "merge_then_split", "taylor_12"])
+@pytest.mark.parametrize("case", ["three_bubbles", "three_bubbles_q27_srt", "merge_then_split",
+                                  "taylor_12"])
 def test_bubbles_parity_fp64(fsl, case, mode):
     if case == "three_bubbles":
         w = inputs.bubbles_in_pool()
+    elif case == "three_bubbles_q27_srt":
+        w = inputs.bubbles_in_pool(q=27, collision="srt", refill="geq")
     elif case == "taylor_12":
         # the Taylor bubble geometry at D = 12: tube of obstacle cells,
         # gravity along z, hydrostatic start, the tail sheds small bubbles
