@@ -904,10 +904,11 @@ __global__ void __launch_bounds__(128) k_stream_collide(Dev d, Geom g, Phys p) {
 
 // Interface cells (list-driven): free-surface boundary condition for PDFs
 // arriving from gas, mass flux, collision, fill level and conversion marks.
-// (16/32-bit path: four blocks per SM at 128 registers; the interface list
-// of a 256^3 drop impact then needs about one wave, 70 instead of 90 us)
+// (16/32-bit path: five blocks per SM at 96 registers, some spilled; the
+// interface list of a 256^3 drop impact then fits in one wave: 90 us at
+// three blocks, 70 at four, and the step 2 % faster again at five)
 template <int Q, class ST>
-__global__ void __launch_bounds__(128, ST::kShift ? 4 : 1) k_stream_collide_if(Dev d, Geom g, Phys p) {
+__global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(Dev d, Geom g, Phys p) {
   using T = typename ST::T;
   using R = typename ST::R;
   constexpr bool SH = ST::kShift;
