@@ -383,7 +383,8 @@ FLOPS_PER_CELL_D3Q27_TRT = 1060
 # each variant; None for a kernel without a capture of its current code.
 TRAFFIC = {("fp16", "pair_r128"): 667.0e6, ("fp16", "pair"): 666.8e6,
            ("fp16", "pair_r96"): 672.7e6, ("fp16", "pair_r80"): 693.9e6,
-           ("fp16", "quad64"): 671.3e6}
+           ("fp16", "quad64"): 671.3e6, ("fp16", "pair_pipe"): 659.9e6,
+           ("fp16", "tma"): 660.8e6, ("fp16", "warp_tma"): 884.1e6}
 
 if __name__ == "__main__":
     main()
