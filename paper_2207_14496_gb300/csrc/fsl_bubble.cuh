@@ -157,7 +157,7 @@ __device__ __forceinline__ bool bub_member(const Geom& g, uint8_t fl) {
 
 // Union-find start: every member points at the first cell of its run of
 // members within its warp (a warp's 32 cells lie in one row, rows being
-// multiples of 64 cells), so a run is one tree before any union; the sums
+// padded to multiples of 32 cells), so a run is one tree before any union; the sums
 // of the new roots (members) and the seen volume of the old roots are
 // cleared.  One cell per thread, no early exit (warp ballots).
 static __global__ void k_bub_init(Dev d, Geom g, int first) {
