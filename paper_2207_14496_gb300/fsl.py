@@ -9,7 +9,6 @@ from __future__ import annotations
 
 import ctypes
 import os
-from dataclasses import dataclass, field
 
 import numpy as np
 
