@@ -10,7 +10,7 @@ mass conservation, resting pool, standing-wave frequency and damping,
 Young-Laplace jump, TRT Poiseuille, hand-built refilling neighbourhoods,
 normal/curvature exactness, free-slip plug flow, Smagorinsky closure, one
 periodic layer = D2Q9, and the bubble model: library labelling, p V through
-compression, merge and split, order-free fixed-point sums).  Parity unpinned
+compression, merge and split, pressures unchanged by a mirrored grid).  Parity unpinned
 (pinned only by oracle = GPU): the Thuerey flux table (R5), excess-mass
 receivers (R3), conflict priority (R6), neighbour means (R7), obstacle
 narrowing of normals (R11), geometry conventions and observables.
@@ -104,8 +104,6 @@ def _load():
         lib.orc_get_types.argtypes = [P, ctypes.c_void_p]
         lib.orc_get_bubbles.argtypes = [P, ctypes.c_void_p, dp]
         lib.orc_bubble_probe.argtypes = [P, ctypes.c_void_p, dp, ctypes.c_int]
-        lib.orc_bubble_range_error.restype = ctypes.c_int
-        lib.orc_bubble_range_error.argtypes = [P]
         for name in ("orc_get_pdfs", "orc_get_phi", "orc_get_mass", "orc_get_kappa"):
             getattr(lib, name).argtypes = [P, dp]
         lib.orc_normal_at.argtypes = [P, ctypes.c_long, dp]
@@ -237,10 +235,6 @@ class Oracle:
         p = np.empty(self.N, dtype=np.float64)
         self.lib.orc_get_bubbles(self.h, lab.ctypes.data_as(ctypes.c_void_p), _dptr(p))
         return lab.reshape(self._grid()), p.reshape(self._grid())
-
-    def bubble_range_error(self) -> bool:
-        """True once a bubble sum term fell outside its fixed-point range."""
-        return bool(self.lib.orc_bubble_range_error(self.h))
 
     def mass(self):
         out = np.empty(self.N, dtype=np.float64)

@@ -59,8 +59,8 @@
  *   R16 plain IEEE round-to-nearest FP64, no contraction.
  *   R23 bubbles: face-connected regions of gas and interface cells (option
  *       32: gas cells alone, interface cells attached), K = p V carried
- *       through merges (added) and splits (shared by volume), sums in fixed
- *       point (see bubble_update).
+ *       through merges (added) and splits (shared by volume); volumes and
+ *       shares of K summed in FP64 in cell order.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -131,10 +131,8 @@ typedef struct {
    * cell), the volume pressure seen by every interface cell; scratch */
   long *blab, *bnew, *bqueue;
   double *bK, *bp;
-  long long *bKnew, *bV, *bVseen; /* fixed-point sums (see bubble_update) */
+  double *bKnew, *bV, *bVseen; /* per-bubble sums, kept at the root cell */
   unsigned char *bhas;
-  int bub_vshift, bub_kshift; /* fixed-point scales 2^vshift, 2^kshift */
-  int bub_range;              /* a term was out of range and counted as 0 */
 } orc_state;
 
 /* ---------------------------------------------------------------- lattice */
@@ -402,46 +400,11 @@ static void update_curvature(orc_state *s) {
  *  - a component without any old cell starts with K = p_V V (the
  *    configuration's volume pressure), as every bubble does initially;
  *  - the volume pressure of an interface cell is K / V of its bubble.
- * The sums are fixed-point integers, so that their value does not depend on
- * the order of summation.  With 2^b the smallest power of two >= the cell
- * count, each cell's w counts as round(w 2^vshift) units, vshift = 62 - b,
- * and each share of K as round(share 2^kshift) units, kshift = vshift - 4
- * (round to nearest, ties to even).  A sum of up to 2^b terms stays below
- * 2^63 while |w| < 2 and every share is below 16 (a share is at most the
- * bubble's pressure, about 1/3 in lattice units); a term outside that range
- * counts as 0 and raises the bub_range flag, and a step in which that
- * happens counts as unstable. */
-static void bub_scales(orc_state *s) {
-  int b = 0;
-  while ((1L << b) < s->N) ++b;
-  s->bub_vshift = 62 - b;
-  s->bub_kshift = s->bub_vshift - 4;
-}
-
-static long long bub_wq(orc_state *s, long x) {
-  double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
-  if (!(fabs(w) < 2.0)) {
-    s->bub_range = 1;
-    return 0;
-  }
-  return llrint(ldexp(w, s->bub_vshift));
-}
-
-static long long bub_kq(orc_state *s, double share) {
-  if (!(fabs(share) < 16.0)) {
-    s->bub_range = 1;
-    return 0;
-  }
-  return llrint(ldexp(share, s->bub_kshift));
-}
-
-static int bubble_update(orc_state *s, int first) {
+ * Every sum is a plain FP64 sum over the cells in index order. */
+static void bubble_update(orc_state *s, int first) {
   const long N = s->N;
   const int q = s->q;
   long *lab = s->bnew;
-  const int range_before = s->bub_range;
-  s->bub_range = 0;
-  bub_scales(s);
   for (long x = 0; x < N; ++x) lab[x] = -1;
   const int gas_only = (s->c.options & ORC_OPT_BUBBLE_GAS_ONLY) != 0;
   /* members: gas cells, and interface cells unless gas_only */
@@ -476,41 +439,38 @@ static int bubble_update(orc_state *s, int first) {
     lab[x] = best;
   }
   for (long x = 0; x < N; ++x) {
-    s->bV[x] = 0;
-    s->bVseen[x] = 0;
-    s->bKnew[x] = 0;
+    s->bV[x] = 0.0;
+    s->bVseen[x] = 0.0;
+    s->bKnew[x] = 0.0;
     s->bhas[x] = 0;
   }
   for (long x = 0; x < N; ++x) {
     if (lab[x] < 0) continue;
-    long long wq = bub_wq(s, x);
-    s->bV[lab[x]] += wq;
-    if (!first && s->blab[x] >= 0) s->bVseen[s->blab[x]] += wq;
+    double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
+    s->bV[lab[x]] += w;
+    if (!first && s->blab[x] >= 0) s->bVseen[s->blab[x]] += w;
   }
   if (!first) {
     for (long x = 0; x < N; ++x) {
       long b = s->blab[x], r = lab[x];
-      if (r < 0 || b < 0 || s->bVseen[b] == 0) continue;
-      double share = s->bK[b] * ((double)bub_wq(s, x) / (double)s->bVseen[b]);
-      s->bKnew[r] += bub_kq(s, share);
+      if (r < 0 || b < 0 || s->bVseen[b] == 0.0) continue;
+      double w = s->type[x] == ORC_GAS ? 1.0 : 1.0 - s->phi[x];
+      s->bKnew[r] += s->bK[b] * (w / s->bVseen[b]);
       s->bhas[r] = 1;
     }
   }
   for (long x = 0; x < N; ++x) {
     long r = lab[x];
     s->blab[x] = r;
-    double V = (r >= 0) ? ldexp((double)s->bV[r], -s->bub_vshift) : 0.0;
-    if (r == x) s->bK[x] = s->bhas[x] ? ldexp((double)s->bKnew[x], -s->bub_kshift) : s->c.p_v * V;
+    double V = (r >= 0) ? s->bV[r] : 0.0;
+    if (r == x) s->bK[x] = s->bhas[x] ? s->bKnew[x] : s->c.p_v * V;
     else s->bK[x] = 0.0;
   }
   for (long x = 0; x < N; ++x) {
     long r = s->blab[x];
-    double V = (r >= 0) ? ldexp((double)s->bV[r], -s->bub_vshift) : 0.0;
+    double V = (r >= 0) ? s->bV[r] : 0.0;
     s->bp[x] = (r >= 0 && V != 0.0) ? s->bK[r] / V : s->c.p_v;
   }
-  const int out = s->bub_range;
-  s->bub_range |= range_before;
-  return out;
 }
 
 void orc_destroy(orc_state *s);
@@ -552,9 +512,9 @@ orc_state *orc_create(const orc_config *cfg) {
   s->bnew = (long *)calloc(N, sizeof(long));
   s->bqueue = (long *)calloc(N, sizeof(long));
   s->bK = (double *)calloc(N, sizeof(double));
-  s->bKnew = (long long *)calloc(N, sizeof(long long));
-  s->bV = (long long *)calloc(N, sizeof(long long));
-  s->bVseen = (long long *)calloc(N, sizeof(long long));
+  s->bKnew = (double *)calloc(N, sizeof(double));
+  s->bV = (double *)calloc(N, sizeof(double));
+  s->bVseen = (double *)calloc(N, sizeof(double));
   s->bp = (double *)calloc(N, sizeof(double));
   s->bhas = (unsigned char *)calloc(N, 1);
   if (!s->type || !s->f || !s->fn || !s->m || !s->phi || !s->rho || !s->kappa || !s->phi_t || !s->cls ||
@@ -994,7 +954,7 @@ static void step_once(orc_state *s) {
 
   /* 6. curvature and (bubble model) volume pressure for the next step's gas density */
   update_curvature(s);
-  if ((s->c.options & ORC_OPT_BUBBLES) && bubble_update(s, 0)) unstable = 1;
+  if (s->c.options & ORC_OPT_BUBBLES) bubble_update(s, 0);
 
   s->step += 1;
   if (unstable && s->unstable_step < 0) s->unstable_step = s->step;
@@ -1121,8 +1081,6 @@ void orc_set_state(orc_state *s, const unsigned char *types, const double *phi, 
  * Writes q PDFs to out.  Used to check the schemes on hand-built cells. */
 /* Bubble bookkeeping alone, for tests: set cell types and fill levels,
  * then run the bubble update (first = 1: fresh bubbles with K = p_V V). */
-int orc_bubble_range_error(const orc_state *s) { return s->bub_range; }
-
 void orc_bubble_probe(orc_state *s, const unsigned char *types, const double *phi, int first) {
   for (long x = 0; x < s->N; ++x) {
     s->type[x] = types[x];

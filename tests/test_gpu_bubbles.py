@@ -1,10 +1,10 @@
 """Bubble model on the GPU (FSL_OPT_BUBBLES) against the CPU oracle: bubble
 labels equal, volume pressures and PDFs within 1e-12 relative, cell types
 bit-exact, through bubbles rising, being compressed, merging and splitting.
-Both sides sum bubble volumes and K in fixed point, so the sums do not depend
-on the order of the GPU's atomics; what is left is the usual FP64 rounding
-difference of the mass exchange, which reaches the pressures through the
-fill levels."""
+The oracle sums bubble volumes and K in FP64 in cell order; the GPU sums them
+in fixed point (independent of the order of its atomics), so the two differ
+by FP64 rounding of the sums, which reaches the PDFs through the gas
+pressure of interface cells."""
 import numpy as np
 import pytest
 

@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from analytic import amplitude, log_decrement, poiseuille, wave_setting
+from analytic import amplitude, log_decrement, omega0, poiseuille, wave_setting
 from paper_2207_14496_gb300 import inputs
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -246,7 +246,11 @@ def test_standing_wave_against_analytic_model():
 
 def test_analytic_model_matches_printed_values():
     """The analytic-model helpers reproduce the paper's printed analytic
-    values (golden file, Sec. 4.1): T*/2 = pi and delta = 0.4961."""
+    values (golden file, Sec. 4.1): the half period T*/2 = pi, measured
+    between consecutive zero crossings of the analytic elevation whose
+    frequency comes from the dispersion relation (with g of the setting),
+    in units of the omega0 that Re fixes; and delta = 0.4961."""
+    from scipy.optimize import brentq
     vals = {}
     with open(os.path.join(GOLDEN, "gravity_wave_analytic.txt")) as fh:
         for line in fh:
@@ -255,7 +259,15 @@ def test_analytic_model_matches_printed_values():
                 vals[k] = float(v)
     for L in (200, 400, 800):
         s = wave_setting(L)
-        half = math.pi / s["omega0"] * s["omega0"]
+        w0 = omega0(s["g"], s["k"], s["d"])
+        elev = lambda t: amplitude(t, 1.0, s["nu"], s["k"], w0)
+        # zero crossings: sign changes on a fine grid over two periods,
+        # refined by bisection
+        ts = np.linspace(0.0, 4.0 * math.pi / s["omega0"], 4001)
+        sv = np.array([elev(t) for t in ts])
+        idx = np.nonzero(np.sign(sv[:-1]) != np.sign(sv[1:]))[0]
+        zs = [brentq(elev, ts[i], ts[i + 1], xtol=1e-12) for i in idx[:2]]
+        half = (zs[1] - zs[0]) * s["omega0"]
         assert abs(half - vals["half_period_tstar"]) < 1e-5
         assert abs(log_decrement(s["nu"], s["k"], s["omega0"]) - vals["log_decrement"]) < 5e-5
 
@@ -381,7 +393,7 @@ def test_refill_uniform_equilibrium_neighbourhood(q, scheme):
     assert np.allclose(out, feq, rtol=1e-14, atol=1e-16)
 
 
-def test_refill_avg_is_mean_and_eq_neq_is_eq_for_equilibrium():
+def test_refill_avg_is_mean_of_linear_field():
     q = 19
     rng = np.random.default_rng(5)
     a, b = rng.uniform(0.01, 0.05, q), rng.uniform(-1e-3, 1e-3, q)
@@ -390,6 +402,78 @@ def test_refill_avg_is_mean_and_eq_neq_is_eq_for_equilibrium():
     # valid neighbours: the liquid ones (x = 5 face, edges with x = 5) and the
     # x = 4 ring; the y-offsets cancel pairwise, so the mean is a + b y_c
     assert np.allclose(out, a + b * 3.0, rtol=1e-13)
+
+
+def _neq_hermite(c, w, A, B, C):
+    """Non-equilibrium populations with zero density and zero momentum: an
+    even second-order Hermite part w_i A:(c_i c_i - I/3) and two odd
+    third-order parts w_i B (c_x c_y^2 - c_x/3) + w_i C (c_y c_z^2 - c_y/3).
+    The odd parts change sign between i and its opposite direction."""
+    H2 = np.einsum("ia,ib->iab", c, c) - np.eye(3) / 3.0
+    even = w * np.einsum("iab,ab->i", H2, A)
+    cx, cy, cz = c[:, 0], c[:, 1], c[:, 2]
+    odd = w * (B * (cx * cy * cy - cx / 3.0) + C * (cy * cz * cz - cy / 3.0))
+    return even + odd
+
+
+def _neq_field(q):
+    """Liquid cells carry f_i(x) = f^eq_i(rho(x), u(x)) + s(x) N_i with
+    linear rho, u and scale s, and N of zero density and momentum, so the
+    moments of f(x) are rho(x), u(x) and its non-equilibrium part is exactly
+    s(x) N_i.  Returns (field, rho, u, s, N)."""
+    probe = _orc(q)
+    c, w, _ = probe.lattice()
+    A = np.array([[2e-3, 1.5e-3, -0.5e-3], [1.5e-3, -1e-3, 0.8e-3], [-0.5e-3, 0.8e-3, -1e-3]])
+    N = _neq_hermite(c, w, A, 3e-3, -2e-3)
+    rho = lambda x, y, z: 1.0 + 0.01 * (x - 4) + 0.004 * (y - 3) - 0.003 * (z - 3)
+    u = lambda x, y, z: (0.01 + 0.002 * (y - 3), -0.004 + 0.001 * (x - 4), 0.003 - 0.0015 * (z - 3))
+    s = lambda x, y, z: 1.0 + 0.3 * (x - 4) + 0.2 * (y - 3) - 0.1 * (z - 3)
+
+    def field(i, x, y, z):
+        out = np.zeros(np.shape(x))
+        for k in np.ndindex(np.shape(x)):
+            p = (x[k], y[k], z[k])
+            out[k] = probe.feq(i, rho(*p), u(*p)) + s(*p) * N[i]
+        return out
+
+    return field, rho, u, s, N
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_refill_eq_neq_copies_neighbour_nonequilibrium(q):
+    """EQ+NEQ (Sec. 3.1, reading R8) on neighbours out of equilibrium: the
+    refilled cell gets f^eq(rho_bar, u_bar) plus the non-equilibrium part of
+    the neighbour x + c^n, direction by direction.  With the normal along +x,
+    c^n = (1, 0, 0) (lowest index among the tied directions).  The field's
+    non-equilibrium part varies from cell to cell and has odd components, so
+    taking it from another neighbour, from the opposite direction or with the
+    wrong sign fails."""
+    field, rho, u, s, N = _neq_field(q)
+    o, idx, new = _refill_setup(q, "eq_neq", field)
+    out = o.refill_probe(idx, new)
+    rb, ub = _mean_state(o, idx, new)
+    expect = _feq_np(o, rb, ub) + s(5, 3, 3) * N
+    assert np.allclose(out, expect, rtol=1e-12, atol=1e-15)
+    # the alternatives differ from the expected values by far more than the
+    # tolerance
+    c, _, opp = o.lattice()
+    assert np.abs(N - N[opp]).max() > 1e-5
+    assert abs(s(5, 4, 3) - s(5, 3, 3)) > 0.1
+
+
+@pytest.mark.parametrize("q", [19, 27])
+def test_refill_eq_neq_literal_mean_copies_neighbour(q):
+    """The literal reading of Sec. 3.1 (f^neq = f(y) - f^eq(rho_bar, u_bar),
+    option NEQ_LITERAL_MEAN) adds and subtracts the same equilibrium, so the
+    refilled PDFs are the stored PDFs of y = x + c^n themselves."""
+    field, rho, u, s, N = _neq_field(q)
+    o, idx, new = _refill_setup(q, "eq_neq", field, options=oracle.OPT_NEQ_LITERAL_MEAN)
+    out = o.refill_probe(idx, new)
+    fy = o.pdfs()[:, 3, 3, 5]
+    assert np.allclose(out, fy, rtol=1e-13, atol=1e-16)
+    # and the default reading does not do that
+    o2, idx2, new2 = _refill_setup(q, "eq_neq", field)
+    assert not np.allclose(o2.refill_probe(idx2, new2), fy, rtol=1e-6, atol=0)
 
 
 def test_refill_ext_exact_for_quadratic_along_normal():
