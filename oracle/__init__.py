@@ -72,9 +72,20 @@ def build(force: bool = False) -> str:
     tmp = _LIB + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
            "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
-    subprocess.run(cmd, check=True)
+    # OpenMP for the order-free per-cell loops where the compiler has it;
+    # without it the same source builds sequential
+    r = subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True, text=True)
+    if r.returncode != 0:
+        subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's order-free per-cell loops (results are bit
+    for bit those of one thread); returns the count in effect (1 without
+    OpenMP)."""
+    return int(_load().orc_set_threads(int(n)))
 
 
 def _load():
@@ -89,6 +100,9 @@ def _load():
         lib.orc_create.argtypes = [ctypes.POINTER(_Config)]
         lib.orc_destroy.argtypes = [P]
         lib.orc_init_fill.argtypes = [P, dp, dp, ctypes.c_void_p, ctypes.c_double]
+        lib.orc_set_threads.restype = ctypes.c_int
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads(1)
         lib.orc_step.restype = ctypes.c_long
         lib.orc_step.argtypes = [P, ctypes.c_long]
         for name in ("orc_num_cells", "orc_step_count", "orc_unstable_step"):

@@ -14,6 +14,15 @@
  * written; nothing is fused, blocked or reordered.  Compile with
  * -ffp-contract=off so that a*b+c is never contracted into an FMA.
  *
+ * Threads: the per-cell loops whose iteration x writes only cell x's own
+ * values and reads nothing that the loop writes (classes, stream/collide,
+ * refilling, finalising conversions, the excess-mass gather, curvature, and
+ * plain copies) may run on several OpenMP
+ * threads (orc_set_threads); every cell's arithmetic is the same in any
+ * order, so the results are bit for bit those of one thread.  Loops that
+ * write neighbours (conversion), sum across cells (lost mass, bubble sums,
+ * observables) or search (bubble labels) always run sequentially.
+ *
  * Sections of the paper followed:
  *   Sec. 2.1  collision (Eq. nm-lbm-collision), streaming (Eq. nm-lbm-streaming),
  *             SRT operator (Eq. nm-lbm-collision-operator, read as relaxation
@@ -65,6 +74,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_GAS 0
 #define ORC_IFACE 1
@@ -368,8 +380,10 @@ static double curvature(const orc_state *s, long x) {
 }
 
 static void update_curvature(orc_state *s) {
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < s->N; ++x) s->kappa[x] = 0.0;
   if (s->c.sigma == 0.0) return;
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < s->N; ++x)
     if (s->type[x] == ORC_IFACE) s->kappa[x] = curvature(s, x);
 }
@@ -708,6 +722,7 @@ static void step_once(orc_state *s) {
   const int thurey = !(s->c.options & ORC_OPT_SIMPLE_FLUX);
 
   /* 1. neighbourhood classes of interface cells from the flags at time t */
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < N; ++x) {
     s->cls[x] = CLS_STD;
     if (s->type[x] != ORC_IFACE) continue;
@@ -721,10 +736,12 @@ static void step_once(orc_state *s) {
     else if (!has_gas && has_liq) s->cls[x] = CLS_NE;
   }
 
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < N; ++x) s->phi_t[x] = s->phi[x];
 
   int unstable = 0;
   /* 2. stream (pull), free-surface and wall boundaries, mass flux, collide */
+#pragma omp parallel for schedule(dynamic, 256) reduction(| : unstable)
   for (long x = 0; x < N; ++x) {
     s->to_liq[x] = 0;
     s->to_gas[x] = 0;
@@ -888,6 +905,7 @@ static void step_once(orc_state *s) {
     }
   }
   /* finalise: Eq. nm-fslbm-excess-mass */
+#pragma omp parallel for schedule(static) reduction(+ : n_fill, n_empty)
   for (long x = 0; x < N; ++x) {
     if (s->to_liq[x]) {
       s->mex[x] = (s->phi[x] - 1.0) * s->rho[x];
@@ -906,12 +924,15 @@ static void step_once(orc_state *s) {
     }
   }
 
-  /* 4. refill new interface cells from their valid neighbours (Sec. 3.1) */
+  /* 4. refill new interface cells from their valid neighbours (Sec. 3.1);
+   * a refilled cell reads only valid (not new) neighbours */
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : n_new)
   for (long x = 0; x < N; ++x) {
     if (!s->is_new[x]) continue;
     refill_cell(s, x);
     n_new++;
   }
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < N; ++x) {
     if (!s->is_new[x]) continue;
     double r = 0.0;
@@ -933,6 +954,7 @@ static void step_once(orc_state *s) {
       s->share[x] = s->mex[x] / (double)n_r;
     }
   }
+#pragma omp parallel for schedule(static)
   for (long x = 0; x < N; ++x) {
     if (s->type[x] != ORC_IFACE) continue;
     int got = 0;
@@ -961,6 +983,18 @@ static void step_once(orc_state *s) {
   s->n_fill = n_fill;
   s->n_empty = n_empty;
   s->n_new = n_new;
+}
+
+/* Threads for the order-free per-cell loops (1 = sequential); returns the
+ * count in effect (1 when built without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+  return n > 0 ? n : 1;
+#else
+  (void)n;
+  return 1;
+#endif
 }
 
 /* Advance n steps; once an instability has been recorded further steps do
