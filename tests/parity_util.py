@@ -26,9 +26,11 @@ def first_mismatch(a: np.ndarray, b: np.ndarray):
 
 
 def compare_state(sim, orc, step: int, rtol: float = 1e-12, atol: float = 1e-15,
-                  label: str = "") -> dict:
+                  label: str = "", atol_fill: float | None = None) -> dict:
     """Flags bit-exact; PDFs (fluid cells), fill level (all cells) and mass
-    (interface cells) within rtol relative.  Returns error statistics."""
+    (interface cells) within rtol relative (plus atol; atol_fill, when given,
+    replaces atol for the fill level and the mass).  Returns error
+    statistics."""
     tg, to = sim.types(), orc.types()
     mm = first_mismatch(tg, to)
     assert mm is None, f"{label} step {step}: cell types differ at (z,y,x)={mm[0]}: gpu {mm[1]} oracle {mm[2]} ({mm[3]} cells)"
@@ -40,13 +42,14 @@ def compare_state(sim, orc, step: int, rtol: float = 1e-12, atol: float = 1e-15,
     bad = err_f > bound_f
     assert not bad.any(), (f"{label} step {step}: PDFs differ, max rel "
                            f"{float((err_f / (np.abs(fo) + 1e-300)).max()):.3e}")
+    af = atol if atol_fill is None else atol_fill
     pg, po = sim.phi(), orc.phi()
     err_p = np.abs(pg - po)
-    assert (err_p <= rtol * np.abs(po) + atol).all(), (
+    assert (err_p <= rtol * np.abs(po) + af).all(), (
         f"{label} step {step}: fill level differs, max abs {float(err_p.max()):.3e}")
     mg, mo = sim.mass()[iface], orc.mass()[iface]
     err_m = np.abs(mg - mo)
-    assert (err_m <= rtol * np.abs(mo) + atol).all(), (
+    assert (err_m <= rtol * np.abs(mo) + af).all(), (
         f"{label} step {step}: interface mass differs, max abs {float(err_m.max()):.3e}")
     return dict(bitwise_pdf=bool((fg == fo).all()), max_pdf_err=float(err_f.max(initial=0.0)),
                 max_phi_err=float(err_p.max(initial=0.0)), n_if=int(iface.sum()))

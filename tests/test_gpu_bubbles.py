@@ -1,10 +1,17 @@
 """Bubble model on the GPU (FSL_OPT_BUBBLES) against the CPU oracle: bubble
-labels equal, volume pressures and PDFs within 1e-12 relative, cell types
-bit-exact, through bubbles rising, being compressed, merging and splitting.
-The oracle sums bubble volumes and K in FP64 in cell order; the GPU sums them
-in fixed point (independent of the order of its atomics), so the two differ
-by FP64 rounding of the sums, which reaches the PDFs through the gas
-pressure of interface cells."""
+labels equal and cell types bit-exact through bubbles rising, being
+compressed, merging and splitting; volume pressures, PDFs, fill levels and
+masses within tolerances derived from the summation order.
+
+The oracle sums bubble volumes and the shares of K = p V in FP64 in cell
+order; the GPU sums them in fixed point (independent of the order of its
+atomics; shares in units of 2^-(58-b) for 2^b >= cells).  The two sums differ
+by rounding, and because K is carried from step to step the difference
+performs a random walk that reaches the PDFs through the gas pressure of
+interface cells.  Measured on the CPU with a fixed-point emulation against the
+plain oracle over these 280-step cases: pressures up to 1e-10 relative (a
+bubble of a few cells), PDFs up to 9.3e-12 relative, fill levels up to
+3.6e-11 absolute; the tolerances below leave a factor of about five."""
 import numpy as np
 import pytest
 
@@ -12,7 +19,9 @@ from paper_2207_14496_gb300 import inputs
 from parity_util import compare_state, make_pair
 
 pytestmark = pytest.mark.gpu
-RTOL = 1e-12
+RTOL_P = 5e-10     # volume pressure, relative
+RTOL = 5e-11       # PDFs, relative
+ATOL_FILL = 2e-10  # fill level and mass, absolute (both of order one)
 
 
 def _compare_bubbles(sim, orc, label):
@@ -22,7 +31,7 @@ def _compare_bubbles(sim, orc, label):
     t = orc.types()
     cells = (t == 1) & (lab_o >= 0)
     p_g = sim.pressure()
-    assert np.allclose(p_g[cells], p_o[cells], rtol=RTOL, atol=0), (
+    assert np.allclose(p_g[cells], p_o[cells], rtol=RTOL_P, atol=0), (
         f"{label}: volume pressures differ, max rel "
         f"{float(np.max(np.abs(p_g[cells] - p_o[cells]) / p_o[cells])):.2e}")
     return len(np.unique(lab_o[lab_o >= 0]))
@@ -57,7 +66,7 @@ def test_bubbles_parity_fp64(fsl, case, mode):
     for k in range(7):
         sim.step(40)
         orc.step(40)
-        compare_state(sim, orc, 40 * (k + 1), RTOL, label=f"{case}/{mode}")
+        compare_state(sim, orc, 40 * (k + 1), RTOL, label=f"{case}/{mode}", atol_fill=ATOL_FILL)
         counts.append(_compare_bubbles(sim, orc, f"{case}/{mode} step {40 * (k + 1)}"))
     assert sim.status()[0] == 0
     if case == "merge_then_split":
