@@ -48,7 +48,10 @@ def load_peaks():
 KERNEL_OF = {"pair": "k_stream_collide_lp", "pair_r128": "k_stream_collide_lp",
              "pair_r96": "k_stream_collide_lp", "pair_r80": "k_stream_collide_lp",
              "tma": "k_stream_collide_bulk", "warp_tma": "k_stream_collide_wtma",
-             "quad64": "k_stream_collide_lp4", "pair_pipe": "k_stream_collide_pp"}
+             "quad64": "k_stream_collide_lp4", "pair_pipe": "k_stream_collide_pp",
+             "cpa": "k_stream_collide_cpa", "cpa_deep": "k_stream_collide_cpa",
+             "cpa_r96": "k_stream_collide_cpa", "seg": "k_stream_collide_seg",
+             "seg_r128": "k_stream_collide_seg"}
 
 # FP64 ALU peak for the bit-exact path, which is built without multiply-add
 # contraction (one FP64 instruction per operation): 152 SMs x 2 FP64 lanes
@@ -125,9 +128,13 @@ def replica_mlups(cells: int, steps: int, ms_max: float, world: int) -> float:
     return world * cells * steps / (ms_max * 1e-3) / 1e6
 
 
-def time_precision(fsl, w, precision, steps, warmup, dev, barrier):
+def time_precision(fsl, w, precision, steps, warmup, dev, barrier, start=0, pre_impact=0):
     """Device-resident timing: CUDA events on the library's stream around K
-    steps (captured CUDA graphs), after W warm-up steps."""
+    steps (captured CUDA graphs), after W warm-up steps.  The state is first
+    advanced `start` steps (untimed) so that the timed window lies in the
+    phase after the drop has hit the pool; with pre_impact > 0 the same
+    number of steps is also timed from step W (before the impact) and
+    reported beside it."""
     import torch
 
     from paper_2207_14496_gb300 import autotune
@@ -135,6 +142,22 @@ def time_precision(fsl, w, precision, steps, warmup, dev, barrier):
     sim = fsl.Sim(w["params"], precision, device=dev)
     sim.init_workload(w)
     sim.set_trace(1)
+    early = None
+    if pre_impact > 0:
+        sim.step(warmup)
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(sim.stream)
+        sim.step(pre_impact)
+        a1.record(sim.stream)
+        torch.cuda.synchronize(dev)
+        t_ms = a0.elapsed_time(a1)
+        early = dict(from_step=warmup, steps=pre_impact, ms_per_step=t_ms / pre_impact,
+                     mlups=sim.N * pre_impact / (t_ms * 1e-3) / 1e6)
+    done = sim.step_count
+    if start > done:
+        sim.step(start - done)
     sim.step(warmup)
     torch.cuda.synchronize(dev)
     # bulk-pass variant picked by the autotuner on the warmed-up state (untimed;
@@ -158,6 +181,7 @@ def time_precision(fsl, w, precision, steps, warmup, dev, barrier):
     ks1 = sim.kernel_stats(reps=10)
     status = sim.status()
     launches = sim.launches_per_step() * steps
+    first = sim.step_count - steps
     del sim
     torch.cuda.empty_cache()
     return dict(ms=ms, ms_per_step=ms / steps, mlups=n_cells * steps / (ms * 1e-3) / 1e6,
@@ -166,7 +190,8 @@ def time_precision(fsl, w, precision, steps, warmup, dev, barrier):
                 n_liquid=0.5 * (ks0["n_liquid"] + ks1["n_liquid"]),
                 n_interface=0.5 * (ks0["n_interface"] + ks1["n_interface"]),
                 clocks=clk.summary(), status=status, launches=launches,
-                variant=tuned["variant"], tuning_ms=tuned["ms"])
+                variant=tuned["variant"], tuning_ms=tuned["ms"], first_step=first,
+                pre_impact=early)
 
 
 def e2e_run(fsl, w, precision, steps, dev, variant="default"):
@@ -197,19 +222,48 @@ def e2e_run(fsl, w, precision, steps, dev, variant="default"):
                 h2d_per_step=h2d / steps, d2h_per_step=d2h / steps, mass=mass)
 
 
-def cpu_baseline(w, steps=1):
-    """The CPU oracle as it stands, single-threaded, on a bounded sample: the
-    full 256^3 workload for `steps` time steps (initial state untimed)."""
+def host_cpu():
+    """Core count (os.cpu_count, as nproc) and CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def time_oracle(w, steps, threads):
+    """Wall time of `steps` oracle steps on `threads` OpenMP threads (the
+    initial state untimed); returns (seconds, threads in effect)."""
     import oracle
-    o = oracle.Oracle(w["params"])
-    o.init_fill(w["phi"], w.get("u0"), None, w["h_ref"])
-    t0 = time.perf_counter()
-    o.step(steps)
-    dt = time.perf_counter() - t0
+    used = oracle.set_threads(threads)
+    try:
+        o = oracle.Oracle(w["params"])
+        o.init_fill(w["phi"], w.get("u0"), None, w["h_ref"])
+        t0 = time.perf_counter()
+        o.step(steps)
+        return time.perf_counter() - t0, used
+    finally:
+        oracle.set_threads(1)
+
+
+def cpu_baseline(w, steps=1):
+    """The CPU oracle as it stands on a bounded sample: the full 256^3 workload
+    for `steps` time steps, on all host cores (its order-free per-cell loops
+    on OpenMP threads) and on one core."""
+    cores, model = host_cpu()
+    dt_all, used = time_oracle(w, steps, cores)
+    dt_one, _ = time_oracle(w, steps, 1)
     n = int(np.prod(w["params"]["shape"]))
-    return dict(value=n * steps / dt / 1e6, unit="MLUPS", cores=1, kind="oracle",
-                sample=f"{steps} step(s) of the full 256^3 D3Q27 drop-impact workload, "
-                       f"single-threaded FP64 C oracle, {dt:.1f} s")
+    return dict(value=n * steps / dt_all / 1e6, unit="MLUPS", cores=used, kind="oracle",
+                cpu_model=model, nproc=cores, single_core=n * steps / dt_one / 1e6,
+                sample=f"{steps} step(s) of the full 256^3 D3Q27 drop-impact workload from its "
+                       f"initial state, FP64 C oracle: {dt_all:.1f} s on {used} threads, "
+                       f"{dt_one:.1f} s on one")
 
 
 def run_reference(args):
@@ -221,6 +275,8 @@ def run_reference(args):
         return
     from paper_2207_14496_gb300 import inputs
     import oracle
+    cores, model = host_cpu()
+    used = oracle.set_threads(cores)
     w = inputs.drop_impact(n=64, pool=24, diameter=10.0, gap=8.0)
     o = oracle.Oracle(w["params"])
     o.init_fill(w["phi"], w.get("u0"), None, w["h_ref"])
@@ -228,16 +284,18 @@ def run_reference(args):
     t0 = time.perf_counter()
     o.step(args.steps)
     dt = time.perf_counter() - t0
+    oracle.set_threads(1)
     n = int(np.prod(w["params"]["shape"]))
     v = n * args.steps / dt / 1e6
     sample = (f"64^3 D3Q27 TRT drop impact (pool 24, drop D=10), {args.steps} oracle steps "
-              f"single-threaded FP64, {dt:.1f} s")
+              f"after {args.warmup}, FP64, {used} OpenMP threads, {dt:.1f} s")
     line = dict(impl="reference", metric=METRIC, value=v, unit="MLUPS", n_gpus=args.gpus,
                 steps=args.steps, warmup=args.warmup, ms_per_step=dt * 1e3 / args.steps,
                 higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f64",
                 data="synthetic", config=dict(workload=WORKLOAD, sample="64^3 scaled drop impact",
-                                              parallelism="cpu-1"),
-                cpu_baseline=dict(value=v, unit="MLUPS", cores=1, kind="oracle", sample=sample),
+                                              parallelism=f"cpu-{used}"),
+                cpu_baseline=dict(value=v, unit="MLUPS", cores=used, kind="oracle", sample=sample,
+                                  cpu_model=model, nproc=cores),
                 e2e=dict(value=v, unit="MLUPS", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
 
@@ -253,6 +311,12 @@ def main():
                     help="steps for the FP64 comparison line (default: steps // 5)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--start", type=int, default=1000,
+                    help="untimed steps before the warm-up (the drop reaches the pool near "
+                         "step 200; the default window lies in the splash that follows)")
+    ap.add_argument("--pre-impact", type=int, default=100,
+                    help="steps also timed from step W, before the impact, for the headline "
+                         "storage (0: skip)")
     ap.add_argument("--size", type=int, default=256,
                     help="edge of the drop-impact cube (256 = the benchmark workload; smaller "
                          "sizes scale pool and drop, for profiling captures)")
@@ -297,7 +361,8 @@ def main():
         k = args.steps
         if p == "fp64":
             k = args.fp64_steps or max(10, args.steps // 5)
-        res[p] = time_precision(fsl, w, p, k, args.warmup, local, barrier)
+        res[p] = time_precision(fsl, w, p, k, args.warmup, local, barrier, start=args.start,
+                                pre_impact=args.pre_impact if p == precs[0] else 0)
         res[p]["steps"] = k
     head = precs[0]
     h = res[head]
@@ -323,7 +388,7 @@ def main():
         ach = r["kernel_bytes"] / (r["kernel_ms"] * 1e-3) / 1e9
         return dict(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
                     frac=ach / peaks["hbm_gbs"], frac_nominal=ach / NOMINAL_HBM_GBS,
-                    traffic=TRAFFIC.get((prec, r["variant"])),
+                    traffic=traffic_of(prec, r["variant"]),
                     kernel=KERNEL_OF.get(r["variant"], "k_stream_collide_lp"),
                     variant=r["variant"], peak_source=peaks["source"])
 
@@ -354,6 +419,7 @@ def main():
             scaling="weak", vs_baseline=None, dtype="f32" if head != "fp64" else "f64",
             storage=head, data="synthetic",
             config=dict(workload=WORKLOAD if args.size == 256 else f"drop_impact_{args.size}",
+                        timed_from_step=h["first_step"],
                         shape=[args.size] * 3, lattice="D3Q27",
                         collision="TRT 3/16", refill="eq", sigma=1e-4, gravity=1e-6,
                         nu=round(inputs.DROP_NU, 9), parallelism=f"replicas{world}",
@@ -367,6 +433,7 @@ def main():
             speedup_vs_fp64=(h["mlups"] / res["fp64"]["mlups"]) if "fp64" in res else None,
             speedup_vs_fp32=(h["mlups"] / res["fp32"]["mlups"]) if "fp32" in res else None,
             stable=not unstable, unstable_steps=unstable or None,
+            pre_impact=h["pre_impact"],
         )
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -379,11 +446,27 @@ def main():
 FLOPS_PER_CELL_D3Q27_TRT = 1060
 # DRAM bytes (read + write) per launch of the bulk kernel on the 256^3
 # workload, from one single-pass ncu capture of the autotuner's launches of
-# each variant; None for a kernel without a capture of its current code.
-TRAFFIC = {("fp16", "pair_r128"): 667.0e6, ("fp16", "pair"): 666.8e6,
-           ("fp16", "pair_r96"): 672.7e6, ("fp16", "pair_r80"): 693.9e6,
-           ("fp16", "quad64"): 671.3e6, ("fp16", "pair_pipe"): 659.9e6,
-           ("fp16", "tma"): 660.8e6, ("fp16", "warp_tma"): 884.1e6}
+# each variant, with the digest of the kernel sources the capture ran
+# (kernel_source_digest); an entry whose digest differs from the sources
+# built now is stale and reported as null.
+TRAFFIC = {}
+KERNEL_SOURCES = ("fsl_kernels.cuh", "fsl_bulk.cuh", "fsl_lattice.cuh", "fsl_internal.h")
+
+
+def kernel_source_digest() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2207_14496_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_of(prec, variant):
+    e = TRAFFIC.get((prec, variant))
+    if e is None or e[1] != kernel_source_digest():
+        return None
+    return e[0]
 
 if __name__ == "__main__":
     main()

@@ -209,14 +209,28 @@ int fsl_launches_per_step(const fsl_handle* h);
  *     shared-memory stages filled by bulk copies, two cells per lane;
  *   PAIR_PIPE (16-bit storages only): as PAIR_R128, but each block walks a
  *     strided sequence of rows and issues the loads of its next row before
- *     colliding the current one (software pipelining over rows).
+ *     colliding the current one (software pipelining over rows);
+ *   CPA, CPA_DEEP, CPA_R96: persistent, tiles of 256 cells with liquid
+ *     (listed by a pre-pass) staged in a ring of shared-memory stages by
+ *     16-byte asynchronous copies (cp.async) that all 128 threads of a block
+ *     issue; the copies of the next tiles are in flight while the block
+ *     collides the current one.  16-bit storages: CPA 3 stages and 4 blocks
+ *     per SM, CPA_DEEP 4 stages and 3 blocks, CPA_R96 (16-bit only) 2 stages
+ *     and 5 blocks (at most 102 registers); FP32: CPA 2 stages and 3 blocks,
+ *     CPA_DEEP 3 stages and 2 blocks;
+ *   SEG, SEG_R128: persistent warps walk the list of 64-cell row segments
+ *     with liquid (listed by a pre-pass), two cells per lane as in PAIR, with
+ *     the flag and PDF loads of a segment in flight together (no warp is
+ *     spent on gas-only rows); at most 96 (SEG) or 128 (SEG_R128) registers.
  * DEFAULT is PAIR_R128; the Python autotuner
  * (paper_2207_14496_gb300.autotune) measures the variants instead.
  * fsl_set_variant drops captured step graphs; FSL_ERR_ARG for an unknown
- * variant and for QUAD_64 or PAIR_PIPE with FP32 storage. */
+ * variant and for QUAD_64, PAIR_PIPE or CPA_R96 with FP32 storage. */
 enum { FSL_VARIANT_DEFAULT = 0, FSL_VARIANT_PAIR = 1, FSL_VARIANT_PAIR_R128 = 2,
        FSL_VARIANT_PAIR_R96 = 3, FSL_VARIANT_TMA = 4, FSL_VARIANT_QUAD_64 = 5,
-       FSL_VARIANT_WARP_TMA = 6, FSL_VARIANT_PAIR_PIPE = 7, FSL_VARIANT_PAIR_R80 = 8 };
+       FSL_VARIANT_WARP_TMA = 6, FSL_VARIANT_PAIR_PIPE = 7, FSL_VARIANT_PAIR_R80 = 8,
+       FSL_VARIANT_CPA = 9, FSL_VARIANT_CPA_DEEP = 10, FSL_VARIANT_CPA_R96 = 11,
+       FSL_VARIANT_SEG = 12, FSL_VARIANT_SEG_R128 = 13 };
 fsl_status fsl_set_variant(fsl_handle* h, int variant);
 int fsl_get_variant(const fsl_handle* h);
 

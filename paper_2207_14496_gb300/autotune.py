@@ -2,8 +2,9 @@
 
 The variants (include/fsl.h, FSL_VARIANT_*) differ in cells per thread (two
 or four), block shape (64 or 128 threads), register cap and the way stored
-values reach the registers (direct loads with warp shuffles, or TMA bulk
-copies into a shared-memory ring).  All give identical results, so the choice
+values reach the registers (direct loads with warp shuffles, TMA bulk copies
+into a shared-memory ring, or 16-byte asynchronous copies by every thread
+into a shared-memory ring).  All give identical results, so the choice
 is purely a matter of speed, and the best one depends on the domain's extent
 along x, its liquid fraction, the lattice and the storage type.  `tune`
 times each candidate on the simulation's current state with the library's
@@ -20,8 +21,9 @@ import os
 
 from . import fsl
 
-CANDIDATES = ("pair", "pair_r128", "pair_r96", "pair_r80", "tma", "quad64", "warp_tma", "pair_pipe")
-HALF_ONLY = ("quad64", "pair_pipe")
+CANDIDATES = ("pair", "pair_r128", "pair_r96", "pair_r80", "tma", "quad64", "warp_tma", "pair_pipe",
+              "cpa", "cpa_deep", "cpa_r96", "seg", "seg_r128")
+HALF_ONLY = ("quad64", "pair_pipe", "cpa_r96")
 
 
 def key_of(sim) -> str:

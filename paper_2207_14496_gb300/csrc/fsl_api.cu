@@ -662,6 +662,7 @@ fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
   // per-step scratch restarts empty: counters zero, claim bytes zero
   c.n_if = c.n_fill = c.n_empty = c.n_new = c.n_l2i = c.n_recv = 0;
   c.n_emptied = c.end_blocks = c.n_tiles = 0;
+  c.tile_next = c.tile_done = 0;
   c.trace_every = h->trace_every;
   c.trace_count = 0;
   c.n_if_next = 0;
@@ -1107,8 +1108,9 @@ fsl_status fsl_lattice_table(int lattice, int* c3q, double* w) {
 int fsl_launches_per_step(const fsl_handle* h) { return h ? h->L->launches_per_step(h->g) : 0; }
 
 fsl_status fsl_set_variant(fsl_handle* h, int variant) {
-  if (!h || variant < FSL_VARIANT_DEFAULT || variant > FSL_VARIANT_PAIR_R80) return FSL_ERR_ARG;
-  if ((variant == FSL_VARIANT_QUAD_64 || variant == FSL_VARIANT_PAIR_PIPE) &&
+  if (!h || variant < FSL_VARIANT_DEFAULT || variant > FSL_VARIANT_SEG_R128) return FSL_ERR_ARG;
+  if ((variant == FSL_VARIANT_QUAD_64 || variant == FSL_VARIANT_PAIR_PIPE ||
+       variant == FSL_VARIANT_CPA_R96) &&
       storage_bytes(h->cfg.precision) != 2)
     return FSL_ERR_ARG;
   h->g.variant = variant;

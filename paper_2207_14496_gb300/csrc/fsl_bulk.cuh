@@ -89,38 +89,52 @@ struct BulkRing {
   static constexpr size_t bytes = stages * stage_bytes + 2 * stages * 8 + 16 * stages + 16;
 };
 
-// List the tiles (TX cells along x of one row) with liquid cells.  One warp
-// per tile, TX / 32 consecutive cells per lane.
+// List the tiles (TX cells along x of one row) with liquid cells.  One thread
+// per tile reads the tile's flag bytes in 16-byte words; a block's tiles are
+// ranked by warp ballots and appended with one atomic per block (the order of
+// the list does not matter to its consumers).  Cells beyond the row's extent
+// hold the gas type.
 template <int TX>
 __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
-  constexpr int CPL = TX / 32;
-  static_assert(CPL == 2 || CPL == 8, "tiles of 64 or 256 cells");
+  static_assert(TX % 32 == 0, "tiles of whole 32-cell rows pieces");
+  __shared__ int warp_n[8];
+  __shared__ unsigned base;
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const long long ntiles = (long long)ntx * g.ny * g.nz;
-  const long long k = (long long)blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (k >= ntiles) return;  // whole warp
-  const int lane = threadIdx.x & 31;
-  const int x0 = (int)(k % ntx) * TX;
-  const long long row = k / ntx;
-  const int xl = x0 + CPL * lane;
-  uint2 f8 = make_uint2(0u, 0u);
-  if (xl < g.sx) {
-    if constexpr (CPL == 8) {
-      f8 = *reinterpret_cast<const uint2*>(d.flags + row * g.sx + xl);
-    } else {
-      const uchar2 b2 = *reinterpret_cast<const uchar2*>(d.flags + row * g.sx + xl);
-      f8.x = (unsigned)b2.x | ((unsigned)b2.y << 8);
+  const long long k = (long long)blockIdx.x * 256 + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool liq = false;
+  if (k < ntiles) {
+    const int x0 = (int)(k % ntx) * TX;
+    const long long row = k / ntx;
+    const int n = (g.sx - x0 < TX ? g.sx - x0 : TX) / 16;  // 16-byte words in the padded row
+    const uint4* w = reinterpret_cast<const uint4*>(d.flags + row * g.sx + x0);
+    for (int q = 0; q < n && !liq; ++q) {
+      const uint4 v = w[q];
+      const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        // a byte whose type bits are T_LIQ: (b & 3) ^ 2 == 0
+        const unsigned t = (u[h] & 0x03030303u) ^ 0x02020202u;
+        liq |= ((t - 0x01010101u) & ~t & 0x80808080u) != 0u;
+      }
     }
   }
-  bool liq = false;
-#pragma unroll
-  for (int b = 0; b < CPL; ++b) {
-    const unsigned byte = ((b < 4 ? f8.x : f8.y) >> (8 * (b & 3))) & 0xffu;
-    const bool in = xl + b < g.nx;
-    liq |= in && (int)(byte & F_TYPE) == T_LIQ;
+  const unsigned m = __ballot_sync(0xffffffffu, liq);
+  if (lane == 0) warp_n[warp] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int tot = 0;
+    for (int w2 = 0; w2 < 8; ++w2) {
+      const int c = warp_n[w2];
+      warp_n[w2] = tot;
+      tot += c;
+    }
+    base = tot ? atomicAdd(&ctrl->n_tiles, (unsigned)tot) : 0u;
   }
-  if (__any_sync(0xffffffffu, liq) && lane == 0) d.l_tiles[atomicAdd(&ctrl->n_tiles, 1u)] = (int)k;
+  __syncthreads();
+  if (liq) d.l_tiles[base + warp_n[warp] + __popc(m & ((1u << lane) - 1u))] = (int)k;
 }
 
 // Update of two neighbouring cells (xa, xa + 1) of row `row` = (y, z), read
@@ -129,16 +143,17 @@ __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
 // plane i on the source row (y - c_iy, z - c_iz) from x = x0 - halo on, `seg`
 // values per direction; li is the staged index of cell xa.  Values are read
 // out of shared memory, both cells collide in packed FP32 and the results go
-// to HBM.  The periodic wrap along x at the two row ends and liquid cells next
-// to a wall or obstacle (per-direction path) read HBM instead.  Returns
-// whether a liquid cell reached |u|^2 >= 1/3.
+// to HBM.  The periodic wrap along x at the two row ends (unless the stage
+// holds the wrapped halos, wrap_staged) and liquid cells next to a wall or
+// obstacle (per-direction path) read HBM instead.  Returns whether a liquid
+// cell reached |u|^2 >= 1/3.
 template <int Q, class ST>
 __device__ __forceinline__ bool bulk_pair(const typename ST::T* __restrict__ A,
                                           typename ST::T* __restrict__ B,
                                           const typename ST::T* stage, int seg, int li, int xa,
                                           int row, int y, int z, uint8_t fl0, uint8_t fl1,
                                           const Dev& d, const Geom& g, const Phys& p,
-                                          const LesLp& les) {
+                                          const LesLp& les, bool wrap_staged = false) {
   using T = typename ST::T;
   constexpr float S = ST::kScaleF;
   const bool liq0 = (fl0 & F_TYPE) == T_LIQ, liq1 = (fl1 & F_TYPE) == T_LIQ;
@@ -162,7 +177,7 @@ __device__ __forceinline__ bool bulk_pair(const typename ST::T* __restrict__ A,
       f[i] = make_float2(ST::ld1s(sg + li - cx), ST::ld1s(sg + li + 1 - cx));
     }
   }
-  if (g.periodic[0] && (xa == 0 || xa + 1 >= g.nx - 1)) {
+  if (!wrap_staged && g.periodic[0] && (xa == 0 || xa + 1 >= g.nx - 1)) {
     // periodic wrap along x: the value comes from the other end of the row
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -454,6 +469,234 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, WarpRing<Q, ST>::min_bloc
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
+// ------------------------------------------------------------------------
+// Block-wide cp.async pipeline.  Persistent CTAs of 128 threads walk the
+// liquid tiles (256 cells of one row, listed by k_tiles<256>) through a ring
+// of S shared-memory stages.  Every thread takes part in
+// filling a stage: per direction i the stage holds the stored values of
+// plane i on the source row (y - c_iy, z - c_iz) for x in [x0 - 8, x0 + 264),
+// cut into 34 pieces of 8 values (16 bytes), followed by the tile's 256 flag
+// bytes; thread t issues the pieces t, t + 128, ... as asynchronous
+// global-to-shared copies (cp.async.cg, one commit group per tile).  Along a
+// periodic x axis whose extent is a multiple of 8 the halo pieces beyond the
+// row ends are copied from the other end of the row, so no cell reads HBM
+// outside the stage (other widths read the wrapped values directly).
+// The loads of S - 1 tiles are in flight while the block collides the
+// current one, and they occupy shared memory, not registers.  A thread's
+// pieces have landed once cp.async.wait_group returns, and the whole stage is
+// visible to the block after the barrier that follows; a second barrier keeps
+// a stage from being refilled before every thread has read it.  Nothing here
+// spins: the waits are the hardware's completion of the copies this thread
+// issued.  The collision of a cell pair is pair_2s (same bits as the other
+// variants).
+//
+// Alignment: piece r of a tile starts at x0 - 8 + 8 r (or at that position
+// moved by +/- nx across the periodic wrap, with nx a multiple of 8), a
+// multiple of 8 elements, and rows are padded to 32 cells, so every piece is
+// 16 bytes at 16-byte-aligned addresses.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int kCpThreads = 128;  // two cells per thread: one tile of 256 cells
+
+template <int Q, class ST, int S>
+struct CpRing {
+  static constexpr int stages = S;
+  static constexpr int epp = 16 / (int)sizeof(typename ST::T);  // values per piece
+  static constexpr int pieces = kBulkSeg / epp;                  // per direction
+  static constexpr size_t seg_bytes = (size_t)kBulkSeg * sizeof(typename ST::T);
+  static constexpr size_t pdf_bytes = (size_t)Q * seg_bytes;
+  static constexpr size_t stage_bytes = pdf_bytes + kBulkTX;  // + flag bytes
+  // stages, the tile coordinates (x0, row, y, z) of each stage, then a ring
+  // of S + 1 tile ids
+  static constexpr size_t bytes = stages * stage_bytes + 16 * stages + 4 * (stages + 1);
+  static_assert(seg_bytes % 16 == 0 && stage_bytes % 16 == 0, "16-byte pieces");
+  static_assert(kBulkSeg % epp == 0 && kBulkHalo % epp == 0, "whole pieces");
+};
+
+// c_iy + 1 and c_iz + 1 of directions 0..26, two bits each (shift 2 i)
+__host__ __device__ constexpr unsigned long long pack_cyz(int a) {
+  unsigned long long v = 0;
+  for (int i = 0; i < 27; ++i) v |= (unsigned long long)(dir_c(i, a) + 1) << (2 * i);
+  return v;
+}
+
+// Update of two neighbouring cells (xa, xa + 1) from a staged tile in two
+// sweeps (collide_2s): the pulled pairs are read out of shared memory once per
+// sweep instead of being held in registers.  Cells with a wall or obstacle in
+// their stencil, and (edge = true) cells at the two ends of a periodic row
+// whose wrapped halo is not staged, take their pulled values from pull_one.
+// Same bits as bulk_pair.  Returns whether a liquid cell reached
+// |u|^2 >= 1/3.
+template <int Q, class ST>
+__device__ __forceinline__ bool pair_2s(const typename ST::T* __restrict__ A,
+                                        typename ST::T* __restrict__ B,
+                                        const typename ST::T* stage, int seg, int li, int xa,
+                                        int row, int y, int z, uint8_t fl0, uint8_t fl1,
+                                        const uint8_t* flags, const Geom& g, const Phys& p,
+                                        const LesLp& les, bool edge) {
+  using T = typename ST::T;
+  constexpr float S = ST::kScaleF;
+  const bool liq0 = (fl0 & F_TYPE) == T_LIQ, liq1 = (fl1 & F_TYPE) == T_LIQ;
+  if (!liq0 && !liq1) return false;
+  const bool near0 = liq0 && ((fl0 & F_NEAR_OBST) || (edge && (xa == 0 || xa == g.nx - 1)));
+  const bool near1 = liq1 && ((fl1 & F_NEAR_OBST) || (edge && xa + 1 == g.nx - 1));
+  const long long P = g.plane;
+  const long long c = (long long)row * g.sx + xa;
+  auto fetch = [&](int i) -> float2 {
+    const int cx = dir_c(i, 0);
+    float2 v;
+    if constexpr (sizeof(T) == 2) {
+      const unsigned short* sg = reinterpret_cast<const unsigned short*>(stage) + (size_t)i * seg;
+      unsigned wv;
+      if (cx == 0) wv = *reinterpret_cast<const unsigned*>(sg + li);
+      else wv = (unsigned)sg[li - cx] | ((unsigned)sg[li + 1 - cx] << 16);
+      v = ST::unpack2(wv);
+    } else {
+      const T* sg = stage + (size_t)i * seg;
+      if (cx == 0) v = *reinterpret_cast<const float2*>(sg + li);
+      else v = make_float2(ST::ld1s(sg + li - cx), ST::ld1s(sg + li + 1 - cx));
+    }
+    if (near0) v.x = pull_one<Q, ST>(A, P, flags, g, xa, y, z, i);
+    if (near1) v.y = pull_one<Q, ST>(A, P, flags, g, xa + 1, y, z, i);
+    return v;
+  };
+  T* out = B + c;
+  auto emit = [&](int i, float2 o) {
+    if (liq0 && liq1) ST::st2(out + i * P, o.x, o.y);
+    else if (liq0) ST::st1(out + i * P, o.x);
+    else ST::st1(out + i * P + 1, o.y);
+  };
+  const bool tr = p.trt != 0;
+  const float lamE = p.f.lam_e, lamO = tr ? p.f.lam_o : p.f.omega;
+  const float pe = p.f.pre_e, po = tr ? p.f.pre_o : p.f.pre_e;
+  const float2 usq = collide_2s<Q>(fetch, emit, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2],
+                                   S, les);
+  return (liq0 && !(usq.x < (float)(1.0 / 3.0))) || (liq1 && !(usq.y < (float)(1.0 / 3.0)));
+}
+
+// Persistent bulk kernel: tiles handed out dynamically, staged by cp.async,
+// collided in two sweeps.  The block takes its next tile from a counter in
+// the control block (thread 0, one tile ahead of the copies that need it), so
+// that slow tiles (rows along a wall) do not leave other SMs idle; the tile
+// ids travel to the other threads through a small ring in shared memory that
+// the two barriers of each iteration order.  The last block to finish resets
+// the counter for the next launch.  Along a periodic x axis with a width that
+// is a multiple of 8 the halos are staged from the other end of the row;
+// otherwise the cells at the row ends, like cells next to a wall, read their
+// pulled values directly (pull_one).
+template <int Q, class ST, int S, int MINB>
+__global__ void __launch_bounds__(kCpThreads, MINB)
+    k_stream_collide_cpa(Dev d, Geom g, Phys p, int ntx) {
+  using T = typename ST::T;
+  using RING = CpRing<Q, ST, S>;
+  constexpr int EPP = RING::epp, NPC = RING::pieces;
+  constexpr int NPIECE = Q * NPC + kBulkTX / 16;  // + flag pieces
+  constexpr int PER_T = (NPIECE + kCpThreads - 1) / kCpThreads;
+  constexpr unsigned long long CY = pack_cyz(1), CZ = pack_cyz(2);
+  extern __shared__ __align__(128) unsigned char smem[];
+  int4* tile_of = reinterpret_cast<int4*>(smem + S * RING::stage_bytes);
+  int* tid_ring = reinterpret_cast<int*>(tile_of + S);  // S + 1 tile ids
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int ntl = (int)ctrl->n_tiles;
+  const int cur = ctrl->step & 1;
+  const T* __restrict__ A = (const T*)d.pdf[cur];
+  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
+  const long long P = g.plane;
+  const int t = threadIdx.x, lane = t & 31;
+  const bool wrapx = g.periodic[0] && (g.nx % EPP) == 0 && g.nx >= kBulkHalo;
+
+  // copies of tile list entry u into stage s (block-uniform call; one commit
+  // group per call, empty past the end of the list)
+  auto issue = [&](int u, int s) {
+    if (u < ntl) {
+      const int k = d.l_tiles[u];
+      const int x0 = (k % ntx) * kBulkTX;
+      const int row = k / ntx;
+      const int y = row % g.ny, z = row / g.ny;
+      unsigned char* stage = smem + (size_t)s * RING::stage_bytes;
+      if (t == 0) tile_of[s] = make_int4(x0, row, y, z);
+      const int ym = y > 0 ? y - 1 : (g.periodic[1] ? g.ny - 1 : y);
+      const int yp = y < g.ny - 1 ? y + 1 : (g.periodic[1] ? 0 : y);
+      const int zm = z > 0 ? z - 1 : (g.periodic[2] ? g.nz - 1 : z);
+      const int zp = z < g.nz - 1 ? z + 1 : (g.periodic[2] ? 0 : z);
+#pragma unroll
+      for (int kk = 0; kk < PER_T; ++kk) {
+        const int c = t + kk * kCpThreads;
+        if (c >= NPIECE) break;
+        if (c < Q * NPC) {
+          const int i = c / NPC, r = c - i * NPC;
+          int xs = x0 - kBulkHalo + EPP * r;
+          if (xs < 0) {
+            if (!wrapx) continue;
+            xs += g.nx;
+          } else if (xs >= g.nx) {
+            if (!wrapx || xs != g.nx) continue;
+            xs = 0;
+          }
+          const int cy = (int)((CY >> (2 * i)) & 3ull) - 1;
+          const int cz = (int)((CZ >> (2 * i)) & 3ull) - 1;
+          const int ys = cy == 0 ? y : (cy == 1 ? ym : yp);
+          const int zs = cz == 0 ? z : (cz == 1 ? zm : zp);
+          const T* src = A + (long long)i * P + (long long)g.sx * (ys + (long long)g.ny * zs) + xs;
+          cp_async16(stage + (size_t)i * RING::seg_bytes + 16 * r, src);
+        } else {
+          const int r = c - Q * NPC;
+          if (x0 + 16 * r < g.sx)
+            cp_async16(stage + RING::pdf_bytes + 16 * r, d.flags + (long long)row * g.sx + x0 + 16 * r);
+        }
+      }
+    }
+    cp_async_commit();
+  };
+
+  if (t == 0)
+    for (int m = 0; m < S; ++m) tid_ring[m] = (int)atomicAdd(&ctrl->tile_next, 1u);
+  __syncthreads();
+#pragma unroll
+  for (int m = 0; m < S - 1; ++m) issue(tid_ring[m], m);
+  const LesLp les = LesLp::of(p);
+  bool bad = false;
+  for (int j = 0;; ++j) {
+    issue(tid_ring[(j + S - 1) % (S + 1)], (j + S - 1) % S);
+    cp_async_wait<S - 1>();  // this thread's pieces of tile j have landed
+    __syncthreads();         // ... and every other thread's
+    const int u = tid_ring[j % (S + 1)];
+    if (u >= ntl) break;     // block-uniform; later ids are larger still
+    if (t == 0) tid_ring[(j + S) % (S + 1)] = (int)atomicAdd(&ctrl->tile_next, 1u);
+    const int s = j % S;
+    const unsigned char* stage = smem + (size_t)s * RING::stage_bytes;
+    const int4 tc = tile_of[s];
+    const int xa = tc.x + 2 * t;
+    const uchar2 f2 = *reinterpret_cast<const uchar2*>(stage + RING::pdf_bytes + 2 * t);
+    const uint8_t fl0 = xa < g.nx ? f2.x : (uint8_t)T_GAS;
+    const uint8_t fl1 = xa + 1 < g.nx ? f2.y : (uint8_t)T_GAS;
+    bad |= pair_2s<Q, ST>(A, B, reinterpret_cast<const T*>(stage), kBulkSeg, kBulkHalo + 2 * t,
+                          xa, tc.y, tc.z, tc.w, fl0, fl1, d.flags, g, p, les,
+                          g.periodic[0] && !wrapx);
+    __syncthreads();  // the stage and the ring slot are read before they are refilled
+  }
+  cp_async_wait<0>();
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+  if (t == 0) {
+    __threadfence();
+    if (atomicAdd(&ctrl->tile_done, 1u) == gridDim.x - 1) {
+      ctrl->tile_next = 0;
+      ctrl->tile_done = 0;
+    }
+  }
 }
 
 }  // namespace fsl

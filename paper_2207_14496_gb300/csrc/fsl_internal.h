@@ -40,6 +40,8 @@ struct Ctrl {
   unsigned end_blocks; // end-of-step blocks finished
   unsigned n_tiles;    // tiles holding liquid cells, listed this step (16/32-bit path)
   unsigned n_if_next;  // interface cells of the next step (appended by k_classify)
+  unsigned tile_next;  // next tile handed out by the dynamically scheduled bulk kernel
+  unsigned tile_done;  // blocks of that kernel finished (the last one resets both)
 };
 
 constexpr int kTraceCapacity = 1 << 16;

@@ -456,6 +456,169 @@ __device__ __forceinline__ V collide_v(const V* f, V* o, float lamE_, float lamO
   return usq;
 }
 
+// The same collision of two cells (V = float2) evaluated in sweeps over the
+// direction pairs instead of from 2Q values held in registers: fetch(i)
+// returns the pulled value pair of direction i (storage units) and is called
+// again in each sweep; emit(i, v) receives the post-collision pair.  Sweep 1
+// forms the density and momentum sums, an optional middle sweep the
+// Smagorinsky momentum flux, and sweep 2 the outputs.  Every accumulator sees
+// the same explicitly rounded operations in the same order as in collide_v,
+// so the results are bit for bit those of collide_v<Q, float2>; only a few
+// moments and per-class constants stay live.  Returns |u|^2 of both cells.
+template <int Q, class Fetch, class Emit>
+__device__ __forceinline__ float2 collide_2s(Fetch&& fetch, Emit&& emit, float lamE_, float lamO_,
+                                             float pe_, float po_, float gx, float gy, float gz,
+                                             float S, const LesLp& les) {
+  using V = float2;
+  constexpr int NP = (Q - 1) / 2;
+  const V z0 = make_float2(0.f, 0.f);
+  V acc = fetch(0);
+  V jx = z0, jy = z0, jz = z0;
+  bool hx = false, hy = false, hz = false;
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int i = 2 * k + 1;
+    const V a = fetch(i), b = fetch(i + 1);
+    const V sp = vadd(a, b), dp = vsub(a, b);
+    acc = vadd(acc, sp);
+    const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
+    if (c0 != 0) { jx = hx ? (c0 == 1 ? vadd(jx, dp) : vsub(jx, dp)) : (c0 == 1 ? dp : vsub(z0, dp)); hx = true; }
+    if (c1 != 0) { jy = hy ? (c1 == 1 ? vadd(jy, dp) : vsub(jy, dp)) : (c1 == 1 ? dp : vsub(z0, dp)); hy = true; }
+    if (c2 != 0) { jz = hz ? (c2 == 1 ? vadd(jz, dp) : vsub(jz, dp)) : (c2 == 1 ? dp : vsub(z0, dp)); hz = true; }
+  }
+  const V drho = vmul(acc, vsplat(1.0f / S, z0));
+  const V rho = vadd(vsplat(1.0f, z0), drho);
+  V kk = rho;
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(Lanes<V>::at(kk, l)));
+    Lanes<V>::at(kk, l) = __fmul_rn(r, 1.0f / S);
+  }
+  const V ux = vfma(jx, kk, vsplat(0.5f * gx, z0));
+  const V uy = vfma(jy, kk, vsplat(0.5f * gy, z0));
+  const V uz = vfma(jz, kk, vsplat(0.5f * gz, z0));
+  const V Fx = vmul(rho, vsplat(gx, z0)), Fy = vmul(rho, vsplat(gy, z0)), Fz = vmul(rho, vsplat(gz, z0));
+  const V usq = vfma(uz, uz, vfma(uy, uy, vmul(ux, ux)));
+  const V uF = vfma(uz, Fz, vfma(uy, Fy, vmul(ux, Fx)));
+  const V cst = vfma(vmul(rho, vsplat(-1.5f, z0)), usq, drho);
+  V lamE = vsplat(lamE_, z0), lamO = vsplat(lamO_, z0), pe = vsplat(pe_, z0), po = vsplat(po_, z0);
+  // the sweeps below read the pulled values again instead of keeping the
+  // first sweep's loads alive
+  asm volatile("" ::: "memory");
+  if (les.cs > 0.f) {
+    V qxx = z0, qyy = z0, qzz = z0, qxy = z0, qxz = z0, qyz = z0;
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+      const int i = 2 * k + 1;
+      const V sp = vadd(fetch(i), fetch(i + 1));
+      const float wS = (float)wgt<Q>(i) * S;
+      const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
+      const V cu = vdot(c0, c1, c2, ux, uy, uz);
+      const V Ac = vmul(vsplat(4.5f * wS, z0), rho), Bcc = vmul(vsplat(wS, z0), cst);
+      const V dn = vsub(sp, vmul(vsplat(2.f, z0), vfma(vmul(Ac, cu), cu, Bcc)));
+      if (c0 != 0) qxx = vadd(qxx, dn);
+      if (c1 != 0) qyy = vadd(qyy, dn);
+      if (c2 != 0) qzz = vadd(qzz, dn);
+      if (c0 * c1 == 1) qxy = vadd(qxy, dn); else if (c0 * c1 == -1) qxy = vsub(qxy, dn);
+      if (c0 * c2 == 1) qxz = vadd(qxz, dn); else if (c0 * c2 == -1) qxz = vsub(qxz, dn);
+      if (c1 * c2 == 1) qyz = vadd(qyz, dn); else if (c1 * c2 == -1) qyz = vsub(qyz, dn);
+    }
+    const V dg = vfma(qzz, qzz, vfma(qyy, qyy, vmul(qxx, qxx)));
+    const V of = vfma(qyz, qyz, vfma(qxz, qxz, vmul(qxy, qxy)));
+    const V qq = vfma(vsplat(2.f, z0), of, dg);
+    V rq = qq, rr = rho;
+#pragma unroll
+    for (int l = 0; l < 2; ++l) {
+      const float qbar = __fmul_rn(__fsqrt_rn(__fmul_rn(2.f, Lanes<V>::at(rq, l))), 1.0f / S);
+      const float t0 = les.tau0;
+      const float arg = __fmaf_rn(t0, t0, __fdiv_rn(__fmul_rn(les.k, qbar), Lanes<V>::at(rr, l)));
+      const float tau = __fmaf_rn(0.5f, __fsub_rn(__fsqrt_rn(arg), t0), t0);
+      const float le = __frcp_rn(tau);
+      const float lo = les.trt ? __frcp_rn(__fadd_rn(0.5f, __fdiv_rn(les.magic, __fsub_rn(tau, 0.5f)))) : le;
+      Lanes<V>::at(lamE, l) = le;
+      Lanes<V>::at(lamO, l) = lo;
+      Lanes<V>::at(pe, l) = __fmaf_rn(-0.5f, le, 1.f);
+      Lanes<V>::at(po, l) = __fmaf_rn(-0.5f, lo, 1.f);
+    }
+  }
+  const V r45 = vmul(vmul(lamE, rho), vsplat(4.5f, z0));
+  const V r3 = vmul(vmul(lamO, rho), vsplat(3.0f, z0));
+  const V kb = vfma(lamE, cst, vmul(vmul(vsplat(-3.0f, z0), pe), uF));
+  V Ap[4], Op[4], K[4], G9[4], G3[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const float wS = (float)wgt<Q>(c == 0 ? 0 : c == 1 ? 1 : c == 2 ? 7 : (Q == 27 ? 19 : 7)) * S;
+    K[c] = vmul(vsplat(wS, z0), kb);
+    if (c == 0) continue;
+    Ap[c] = vmul(vsplat(wS, z0), r45);
+    Op[c] = vmul(vsplat(wS, z0), r3);
+    G9[c] = vmul(vsplat(9.0f * wS, z0), pe);
+    G3[c] = vmul(vsplat(3.0f * wS, z0), po);
+  }
+  const V al = vfma(vsplat(-0.5f, z0), lamE, vsplat(0.5f, z0));
+  const V be = vfma(vsplat(-0.5f, z0), lamO, vsplat(0.5f, z0));
+  asm volatile("" ::: "memory");
+  emit(0, vfma(vsub(vsplat(1.0f, z0), lamE), fetch(0), K[0]));
+#pragma unroll
+  for (int k = 0; k < NP; ++k) {
+    const int i = 2 * k + 1;
+    const int c = len2(i);
+    const V a = fetch(i), b = fetch(i + 1);
+    const V sp = vadd(a, b), dp = vsub(a, b);
+    const int c0 = dir_c(i, 0), c1 = dir_c(i, 1), c2 = dir_c(i, 2);
+    const V cu = vdot(c0, c1, c2, ux, uy, uz);
+    const V cF = vdot(c0, c1, c2, Fx, Fy, Fz);
+    const V E = vfma(vfma(Ap[c], cu, vmul(G9[c], cF)), cu, K[c]);
+    const V D = vfma(Op[c], cu, vmul(G3[c], cF));
+    const V Pp = vfma(al, sp, E);
+    const V Mm = vfma(be, dp, D);
+    emit(i, vadd(Pp, Mm));
+    emit(i + 1, vsub(Pp, Mm));
+  }
+  return usq;
+}
+
+// pull_liquid's near-obstacle path for the liquid cell (x, y, z), out of line
+// so that the rare cells next to a wall cost the fast path no registers.
+template <int Q, class ST>
+__device__ __noinline__ void pull_near(const typename ST::T* __restrict__ A, long long plane,
+                                       const uint8_t* flags, const Geom& g, int x, int y, int z,
+                                       typename ST::R* fin) {
+  Nbr nb;
+  nb.setup(g, x, y, z);
+  pull_liquid<Q, ST>(A, plane, flags, nb, x + g.sx * (y + g.ny * z), true, fin);
+}
+
+// Pulled value of direction i at a cell next to a wall or obstacle, in
+// storage units: f*_i of the source cell x - c_i (or its mirror image across
+// free-slip walls, in the mirrored direction), f*_(opp i) of the cell itself
+// (halfway bounce-back) where the source is a no-slip wall or an obstacle;
+// the same values as pull_liquid's near-obstacle path.  Out of line: used by
+// the rare cells with a wall in their stencil.
+template <int Q, class ST>
+__device__ __noinline__ float pull_one(const typename ST::T* __restrict__ A, long long plane,
+                                       const uint8_t* flags, const Geom& g, int x, int y, int z,
+                                       int i) {
+  const int c = x + g.sx * (y + g.ny * z);
+  int a = x - rc(i, 0), b = y - rc(i, 1), e = z - rc(i, 2);
+  int crossed = 0;
+  if (a < 0 || a >= g.nx) { if (g.periodic[0]) a = a < 0 ? g.nx - 1 : 0; else crossed |= 1; }
+  if (b < 0 || b >= g.ny) { if (g.periodic[1]) b = b < 0 ? g.ny - 1 : 0; else crossed |= 2; }
+  if (e < 0 || e >= g.nz) { if (g.periodic[2]) e = e < 0 ? g.nz - 1 : 0; else crossed |= 4; }
+  int dir = i;
+  if (crossed) {
+    if ((crossed & g.free_slip) != crossed) return ST::ld1(A + opp(i) * plane + c);
+    if (crossed & 1) a = x;
+    if (crossed & 2) b = y;
+    if (crossed & 4) e = z;
+    dir = mirror_dir<Q>(i, crossed);
+  }
+  const int n = a + g.sx * (b + g.ny * e);
+  if ((flags[n] & F_TYPE) == T_OBST) return ST::ld1(A + opp(i) * plane + c);
+  return ST::ld1(A + dir * plane + n);
+}
+
 template <int Q>
 __device__ __forceinline__ float collide_lp(const float* f, float* o, float lamE, float lamO,
                                             float pe, float po, float gx, float gy, float gz,
@@ -464,28 +627,27 @@ __device__ __forceinline__ float collide_lp(const float* f, float* o, float lamE
   return collide_v<Q, float>(f, o, lamE, lamO, pe, po, gx, gy, gz, S, les);
 }
 
-// Bulk pass of the 16/32-bit path: two cells (x0, x0+1) per thread, pairs of
-// PDFs loaded as one aligned 4/8-byte word per direction; PDFs pulled from
-// x -/+ 1 come from the neighbouring lane by a warp shuffle (one extra
-// scalar load at the warp's edge or at a periodic wrap).  Liquid cells next
-// to a wall or obstacle take the per-direction bounce-back path.
-template <int Q, class ST, int BT, int MINB, bool PACKED>
-__global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, Phys p) {
+// Update of two cells (x0, x0 + 1) of row (y, z) by one thread of a warp whose
+// 32 threads cover 64 consecutive cells of that row: pairs of PDFs loaded as
+// one aligned 4/8-byte word per direction; PDFs pulled from x -/+ 1 come from
+// the neighbouring lane by a warp shuffle (one extra scalar load at the
+// warp's edge or at a periodic wrap).  Liquid cells next to a wall or
+// obstacle take the per-direction bounce-back path.  GATE: the warp reads the
+// flag bytes first and leaves without loading PDFs when it holds no liquid
+// cell (grids over every cell); without GATE the PDF loads are issued
+// together with the flag loads (warps that walk a list of segments with
+// liquid).  Warp-uniform call; returns whether a liquid cell reached
+// |u|^2 >= 1/3.
+template <int Q, class ST, bool PACKED, bool GATE>
+__device__ __forceinline__ bool pair_update(const Dev& d, const Geom& g, const Phys& p, int x0,
+                                            int y, int z, int lane) {
   using T = typename ST::T;
   constexpr float S = ST::kScaleF;
-  Ctrl* ctrl = d.ctrl;
-  if (frozen(ctrl)) return;
-  const int cur = ctrl->step & 1;
+  const int cur = d.ctrl->step & 1;
   const T* __restrict__ A = (const T*)d.pdf[cur];
   T* __restrict__ B = (T*)d.pdf[cur ^ 1];
   const long long P = g.plane;
   const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-  // narrow domains put several rows in one block (blockDim.x is a multiple
-  // of 32, so every warp lies in one row)
-  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
-  if (y >= g.ny) return;
   const int row = g.sx * (y + g.ny * z);
   const bool in_row = x0 < g.sx;
   const int xc = in_row ? x0 : g.sx - 2;  // clamped pair start for addressing
@@ -497,9 +659,10 @@ __global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, P
   }
   const int t0 = fl0 & F_TYPE, t1 = fl1 & F_TYPE;
   const bool liq0 = t0 == T_LIQ, liq1 = t1 == T_LIQ;
-  if (!__any_sync(FULL, liq0 || liq1)) return;
+  if (GATE && !__any_sync(FULL, liq0 || liq1)) return false;
   // rows of the y/z neighbours (a wall side maps to the cell's own row: such
-  // cells are near-obstacle and never use the fast values)
+  // cells are near-obstacle and never use the fast values); row offsets fit
+  // 32 bits (fewer than 2^31 cells), the plane offset i P is uniform
   int Yr[3], Zr[3];
   Yr[1] = y; Zr[1] = z;
   Yr[0] = y > 0 ? y - 1 : (g.periodic[1] ? g.ny - 1 : y);
@@ -515,7 +678,7 @@ __global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, P
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
-    const T* base = A + i * P + (long long)g.sx * (Yr[1 - cy] + g.ny * Zr[1 - cz]);
+    const T* base = (A + i * P) + g.sx * (Yr[1 - cy] + g.ny * Zr[1 - cz]);
     const float2 v = ST::ld2(base + xc);
     if (cx == 0) {
       f[i] = v;
@@ -529,19 +692,36 @@ __global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, P
       if (wrap0) f[i].x = ST::ld1(base);
     }
   }
-  if ((liq0 && (fl0 & F_NEAR_OBST)) || (liq1 && (fl1 & F_NEAR_OBST))) {
+  // cells with a wall or obstacle in their stencil.  Domain walls only (no
+  // obstacle cell, no free-slip wall): a PDF whose source lies beyond a wall
+  // is the cell's own f*_(opp i) (halfway bounce-back), every other pulled
+  // value above came from the right row already.  Otherwise the general
+  // per-direction path, out of line.
+  const bool walls_only = !g.has_obst && !g.free_slip;
+  if (walls_only && ((liq0 && (fl0 & F_NEAR_OBST)) || (liq1 && (fl1 & F_NEAR_OBST)))) {
+    const bool wl0 = !g.periodic[0] && x0 == 0, wr1 = !g.periodic[0] && x0 + 2 >= g.nx;
+    const bool wr0 = !g.periodic[0] && x0 + 1 >= g.nx;
+    const bool ylo = !g.periodic[1] && y == 0, yhi = !g.periodic[1] && y == g.ny - 1;
+    const bool zlo = !g.periodic[2] && z == 0, zhi = !g.periodic[2] && z == g.nz - 1;
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
+      // the source x - c_i crosses a wall in y or z (both cells), or in x
+      const bool yz = (cy == 1 && ylo) || (cy == -1 && yhi) || (cz == 1 && zlo) || (cz == -1 && zhi);
+      const bool c0 = yz || (cx == 1 && wl0) || (cx == -1 && wr0);
+      const bool c1 = yz || (cx == -1 && wr1);
+      if (liq0 && (fl0 & F_NEAR_OBST) && c0) f[i].x = ST::ld1(A + opp(i) * P + row + x0);
+      if (liq1 && (fl1 & F_NEAR_OBST) && c1) f[i].y = ST::ld1(A + opp(i) * P + row + x0 + 1);
+    }
+  } else if ((liq0 && (fl0 & F_NEAR_OBST)) || (liq1 && (fl1 & F_NEAR_OBST))) {
     float t[Q];
     if (liq0 && (fl0 & F_NEAR_OBST)) {
-      Nbr nb;
-      nb.setup(g, x0, y, z);
-      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0, true, t);
+      pull_near<Q, ST>(A, P, d.flags, g, x0, y, z, t);
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[i].x = t[i] * S;
     }
     if (liq1 && (fl1 & F_NEAR_OBST)) {
-      Nbr nb;
-      nb.setup(g, x0 + 1, y, z);
-      pull_liquid<Q, ST>(A, P, d.flags, nb, row + x0 + 1, true, t);
+      pull_near<Q, ST>(A, P, d.flags, g, x0 + 1, y, z, t);
 #pragma unroll
       for (int i = 0; i < Q; ++i) f[i].y = t[i] * S;
     }
@@ -582,9 +762,52 @@ __global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, P
 #pragma unroll
     for (int i = 0; i < Q; ++i) ST::st1(out + i * P + 1, f[i].y);
   }
-  if (__any_sync(FULL, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+  return bad;
 }
 
+// Bulk pass of the 16/32-bit path over every cell: two cells per thread (see
+// pair_update), a block of 128 threads covering 256 cells of a row, or
+// several rows of a narrower domain (blockDim.x is a multiple of 32, so every
+// warp lies in one row); warps without liquid cells leave after their flags.
+template <int Q, class ST, int BT, int MINB, bool PACKED>
+__global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, Phys p) {
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int lane = threadIdx.x & 31;
+  const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int y = blockIdx.y * blockDim.y + threadIdx.y, z = blockIdx.z;
+  if (y >= g.ny) return;
+  const bool bad = pair_update<Q, ST, PACKED, true>(d, g, p, x0, y, z, lane);
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
+// Bulk pass over the list of 64-cell row segments with liquid (k_tiles<64>):
+// persistent warps walk the list with a grid stride, one segment (two cells
+// per lane, pair_update without the flag gate) per iteration; the list entry
+// of the next iteration is loaded one iteration ahead.  No gas-only warp is
+// launched and a warp's flag and PDF loads are in flight together, so every
+// segment costs one memory round trip.
+template <int Q, class ST, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_stream_collide_seg(Dev d, Geom g, Phys p, int ntx) {
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int ntl = (int)ctrl->n_tiles;
+  const int lane = threadIdx.x & 31;
+  const int tw = gridDim.x * (blockDim.x >> 5);
+  int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int seg = k < ntl ? d.l_tiles[k] : 0;
+  bool bad = false;
+  while (k < ntl) {
+    const int kn = k + tw;
+    const int segn = kn < ntl ? d.l_tiles[kn] : 0;
+    const int x0 = (seg % ntx) * 64 + 2 * lane;
+    const int row = seg / ntx;
+    bad |= pair_update<Q, ST, true, false>(d, g, p, x0, row % g.ny, row / g.ny, lane);
+    k = kn;
+    seg = segn;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
 
 // Bulk pass of the 16-bit storages with four cells per thread: the four
 // stored values of each direction arrive as one aligned 8-byte load and stay
@@ -2055,22 +2278,47 @@ struct Kernels {
   // resolved bulk-kernel variant of the 16/32-bit path
   static int variant_of(const Geom& g) {
     constexpr bool half = sizeof(typename ST::T) == 2;
-    if ((g.variant >= 1 && g.variant <= 4) || g.variant == 6 || g.variant == 8) return g.variant;
-    if ((g.variant == 5 || g.variant == 7) && half) return g.variant;
+    if ((g.variant >= 1 && g.variant <= 4) || g.variant == 6 || g.variant == 8 || g.variant == 9 ||
+        g.variant == 10 || g.variant == 12 || g.variant == 13)
+      return g.variant;
+    if ((g.variant == 5 || g.variant == 7 || g.variant == 11) && half) return g.variant;
     return 2;
+  }
+  // variants that walk the list of liquid tiles of 256 cells
+  static bool uses_tiles256(int v) { return v == 4 || v == 9 || v == 10 || v == 11; }
+  // persistent cp.async pipeline with S stages and at least MINB blocks per SM
+  template <int S, int MINB>
+  static cudaError_t launch_cpa(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
+    static int grid = 0;
+    constexpr size_t smem = CpRing<Q, ST, S>::bytes;
+    if (grid == 0) {
+      cudaError_t e = cudaFuncSetAttribute(k_stream_collide_cpa<Q, ST, S, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0, dev = 0, sms = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_cpa<Q, ST, S, MINB>,
+                                                        kCpThreads, smem);
+      if (e != cudaSuccess) return e;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      grid = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    const int ntx = (g.nx + kBulkTX - 1) / kBulkTX;
+    k_stream_collide_cpa<Q, ST, S, MINB><<<grid, kCpThreads, smem, s>>>(d, g, p, ntx);
+    return cudaGetLastError();
   }
   static cudaError_t pre_bulk(const Dev& d, const Geom& g, const Phys&, cudaStream_t s) {
     if constexpr (ST::kShift) {
-      if (variant_of(g) == 4) {
+      if (uses_tiles256(variant_of(g))) {
         const int ntx = (g.nx + kBulkTX - 1) / kBulkTX;
         const long long ntiles = (long long)ntx * g.ny * g.nz;
-        k_tiles<kBulkTX><<<(unsigned)((ntiles + 7) / 8), 256, 0, s>>>(d, g, ntx);
+        k_tiles<kBulkTX><<<(unsigned)((ntiles + 255) / 256), 256, 0, s>>>(d, g, ntx);
         return cudaGetLastError();
       }
-      if (variant_of(g) == 6) {
+      if (variant_of(g) == 6 || variant_of(g) == 12 || variant_of(g) == 13) {
         const int ntx = (g.nx + kWarpTX - 1) / kWarpTX;
         const long long ntiles = (long long)ntx * g.ny * g.nz;
-        k_tiles<kWarpTX><<<(unsigned)((ntiles + 7) / 8), 256, 0, s>>>(d, g, ntx);
+        k_tiles<kWarpTX><<<(unsigned)((ntiles + 255) / 256), 256, 0, s>>>(d, g, ntx);
         return cudaGetLastError();
       }
     }
@@ -2079,6 +2327,34 @@ struct Kernels {
   static cudaError_t stream_collide(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
     if constexpr (ST::kShift) {
       const int v = variant_of(g);
+      constexpr bool half = sizeof(typename ST::T) == 2;
+      if (v == 12 || v == 13) {
+        // persistent warps over the 64-cell segment list: as many blocks as fit
+        static int grid12 = 0, grid13 = 0;
+        int& grid = v == 12 ? grid12 : grid13;
+        if (grid == 0) {
+          int per_sm = 0, dev = 0, sms = 0;
+          cudaError_t e = v == 12
+              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_seg<Q, ST, 5>, 128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_seg<Q, ST, 4>, 128, 0);
+          if (e != cudaSuccess) return e;
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          grid = (per_sm > 0 ? per_sm : 1) * sms;
+        }
+        const int ntx = (g.nx + kWarpTX - 1) / kWarpTX;
+        if (v == 12) k_stream_collide_seg<Q, ST, 5><<<grid, 128, 0, s>>>(d, g, p, ntx);
+        else k_stream_collide_seg<Q, ST, 4><<<grid, 128, 0, s>>>(d, g, p, ntx);
+        return cudaGetLastError();
+      }
+      if constexpr (half) {
+        if (v == 9) return launch_cpa<2, 6>(d, g, p, s);
+        if (v == 10) return launch_cpa<3, 4>(d, g, p, s);
+        if (v == 11) return launch_cpa<2, 7>(d, g, p, s);
+      } else {
+        if (v == 9) return launch_cpa<2, 3>(d, g, p, s);
+        if (v == 10) return launch_cpa<3, 2>(d, g, p, s);
+      }
       if (v == 4) {
         // persistent grid: as many CTAs as fit on the GPU (queried once)
         static int grid = 0;
@@ -2158,7 +2434,12 @@ struct Kernels {
   // gather, classify, end of step; six more with the bubble model
   static int launches(const Geom& g) {
     const int bub = g.bubbles ? 6 : 0;
-    if constexpr (ST::kShift) return ((variant_of(g) == 4 || variant_of(g) == 6) ? 11 : 10) + bub;
+    if constexpr (ST::kShift)
+      return ((uses_tiles256(variant_of(g)) || variant_of(g) == 6 || variant_of(g) == 12 ||
+               variant_of(g) == 13)
+                  ? 11
+                  : 10) +
+             bub;
     return 10 + bub;
   }
   static const Launch* table() {
