@@ -51,7 +51,8 @@ KERNEL_OF = {"pair": "k_stream_collide_lp", "pair_r128": "k_stream_collide_lp",
              "quad64": "k_stream_collide_lp4", "pair_pipe": "k_stream_collide_pp",
              "cpa": "k_stream_collide_cpa", "cpa_deep": "k_stream_collide_cpa",
              "cpa_r96": "k_stream_collide_cpa", "seg": "k_stream_collide_seg",
-             "seg_r128": "k_stream_collide_seg"}
+             "seg_r128": "k_stream_collide_seg", "cell": "k_stream_collide_c1",
+             "cell_r80": "k_stream_collide_c1", "tma_r96": "k_stream_collide_bulk"}
 
 # FP64 ALU peak for the bit-exact path, which is built without multiply-add
 # contraction (one FP64 instruction per operation): 152 SMs x 2 FP64 lanes

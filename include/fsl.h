@@ -221,16 +221,22 @@ int fsl_launches_per_step(const fsl_handle* h);
  *   SEG, SEG_R128: persistent warps walk the list of 64-cell row segments
  *     with liquid (listed by a pre-pass), two cells per lane as in PAIR, with
  *     the flag and PDF loads of a segment in flight together (no warp is
- *     spent on gas-only rows); at most 96 (SEG) or 128 (SEG_R128) registers.
+ *     spent on gas-only rows); at most 96 (SEG) or 128 (SEG_R128) registers;
+ *   CELL, CELL_R80: as SEG, but one cell per thread: one value loaded per
+ *     direction straight from the source cell (no shuffles), the collision
+ *     on one cell in FP32, at most 64 (CELL) or 80 (CELL_R80) registers;
+ *   TMA_R96 (16-bit storages only): as TMA with three stages and four blocks
+ *     per SM (at most 102 registers), sixteen consumer warps per SM.
  * DEFAULT is PAIR_R128; the Python autotuner
  * (paper_2207_14496_gb300.autotune) measures the variants instead.
  * fsl_set_variant drops captured step graphs; FSL_ERR_ARG for an unknown
- * variant and for QUAD_64, PAIR_PIPE or CPA_R96 with FP32 storage. */
+ * variant and for QUAD_64, PAIR_PIPE, CPA_R96 or TMA_R96 with FP32 storage. */
 enum { FSL_VARIANT_DEFAULT = 0, FSL_VARIANT_PAIR = 1, FSL_VARIANT_PAIR_R128 = 2,
        FSL_VARIANT_PAIR_R96 = 3, FSL_VARIANT_TMA = 4, FSL_VARIANT_QUAD_64 = 5,
        FSL_VARIANT_WARP_TMA = 6, FSL_VARIANT_PAIR_PIPE = 7, FSL_VARIANT_PAIR_R80 = 8,
        FSL_VARIANT_CPA = 9, FSL_VARIANT_CPA_DEEP = 10, FSL_VARIANT_CPA_R96 = 11,
-       FSL_VARIANT_SEG = 12, FSL_VARIANT_SEG_R128 = 13 };
+       FSL_VARIANT_SEG = 12, FSL_VARIANT_SEG_R128 = 13, FSL_VARIANT_CELL = 14,
+       FSL_VARIANT_CELL_R80 = 15, FSL_VARIANT_TMA_R96 = 16 };
 fsl_status fsl_set_variant(fsl_handle* h, int variant);
 int fsl_get_variant(const fsl_handle* h);
 

@@ -1108,9 +1108,9 @@ fsl_status fsl_lattice_table(int lattice, int* c3q, double* w) {
 int fsl_launches_per_step(const fsl_handle* h) { return h ? h->L->launches_per_step(h->g) : 0; }
 
 fsl_status fsl_set_variant(fsl_handle* h, int variant) {
-  if (!h || variant < FSL_VARIANT_DEFAULT || variant > FSL_VARIANT_SEG_R128) return FSL_ERR_ARG;
+  if (!h || variant < FSL_VARIANT_DEFAULT || variant > FSL_VARIANT_TMA_R96) return FSL_ERR_ARG;
   if ((variant == FSL_VARIANT_QUAD_64 || variant == FSL_VARIANT_PAIR_PIPE ||
-       variant == FSL_VARIANT_CPA_R96) &&
+       variant == FSL_VARIANT_CPA_R96 || variant == FSL_VARIANT_TMA_R96) &&
       storage_bytes(h->cfg.precision) != 2)
     return FSL_ERR_ARG;
   h->g.variant = variant;

@@ -79,9 +79,9 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
 }
 
 // ring depth and shared-memory layout per storage type
-template <int Q, class ST>
+template <int Q, class ST, int NS = (sizeof(typename ST::T) == 2 ? 4 : 3)>
 struct BulkRing {
-  static constexpr int stages = sizeof(typename ST::T) == 2 ? 4 : 3;
+  static constexpr int stages = NS;
   static constexpr size_t pdf_bytes = (size_t)Q * kBulkSeg * sizeof(typename ST::T);
   static constexpr size_t stage_bytes = pdf_bytes + kBulkTX;  // + flag bytes
   // stages, then full[stages] and empty[stages] barriers, the tile
@@ -143,17 +143,20 @@ __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
 // plane i on the source row (y - c_iy, z - c_iz) from x = x0 - halo on, `seg`
 // values per direction; li is the staged index of cell xa.  Values are read
 // out of shared memory, both cells collide in packed FP32 and the results go
-// to HBM.  The periodic wrap along x at the two row ends (unless the stage
-// holds the wrapped halos, wrap_staged) and liquid cells next to a wall or
-// obstacle (per-direction path) read HBM instead.  Returns whether a liquid
-// cell reached |u|^2 >= 1/3.
+// to HBM.  The periodic wrap along x at the two row ends: wrap = 0, read from
+// HBM; 1, the stage holds the wrapped halos; 2, the stage holds the whole row
+// (x0 = 0, nx <= the tile width) and the value comes from its other end.
+// Liquid cells next to a domain wall (no obstacle cell, no free-slip wall)
+// take the halfway bounce-back value for the directions that cross the wall;
+// next to an obstacle or a free-slip wall the per-direction path reads HBM.
+// Returns whether a liquid cell reached |u|^2 >= 1/3.
 template <int Q, class ST>
 __device__ __forceinline__ bool bulk_pair(const typename ST::T* __restrict__ A,
                                           typename ST::T* __restrict__ B,
                                           const typename ST::T* stage, int seg, int li, int xa,
                                           int row, int y, int z, uint8_t fl0, uint8_t fl1,
                                           const Dev& d, const Geom& g, const Phys& p,
-                                          const LesLp& les, bool wrap_staged = false) {
+                                          const LesLp& les, int wrap = 0) {
   using T = typename ST::T;
   constexpr float S = ST::kScaleF;
   const bool liq0 = (fl0 & F_TYPE) == T_LIQ, liq1 = (fl1 & F_TYPE) == T_LIQ;
@@ -177,7 +180,19 @@ __device__ __forceinline__ bool bulk_pair(const typename ST::T* __restrict__ A,
       f[i] = make_float2(ST::ld1s(sg + li - cx), ST::ld1s(sg + li + 1 - cx));
     }
   }
-  if (!wrap_staged && g.periodic[0] && (xa == 0 || xa + 1 >= g.nx - 1)) {
+  if (wrap == 2 && g.periodic[0] && (xa == 0 || xa + 1 >= g.nx - 1)) {
+    // the whole row is staged: cell x sits at li - (xa - x)
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int cx = dir_c(i, 0);
+      if (cx == 0) continue;
+      const T* sg = stage + (size_t)i * seg;
+      if (cx == 1 && xa == 0) f[i].x = ST::ld1s(sg + li + g.nx - 1);
+      if (cx == -1 && xa == g.nx - 1) f[i].x = ST::ld1s(sg + li - xa);
+      if (cx == -1 && xa + 1 == g.nx - 1) f[i].y = ST::ld1s(sg + li - xa);
+    }
+  }
+  if (wrap == 0 && g.periodic[0] && (xa == 0 || xa + 1 >= g.nx - 1)) {
     // periodic wrap along x: the value comes from the other end of the row
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -192,14 +207,25 @@ __device__ __forceinline__ bool bulk_pair(const typename ST::T* __restrict__ A,
     }
   }
   const long long c = (long long)row * g.sx + xa;
+  const bool near0 = liq0 && (fl0 & F_NEAR_OBST), near1 = liq1 && (fl1 & F_NEAR_OBST);
+  if ((near0 || near1) && !g.has_obst && !g.free_slip) {
+    const bool wl0 = !g.periodic[0] && xa == 0, wr0 = !g.periodic[0] && xa + 1 >= g.nx;
+    const bool wr1 = !g.periodic[0] && xa + 2 >= g.nx;
+    const bool ylo = !g.periodic[1] && y == 0, yhi = !g.periodic[1] && y == g.ny - 1;
+    const bool zlo = !g.periodic[2] && z == 0, zhi = !g.periodic[2] && z == g.nz - 1;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    const uint8_t fh = h ? fl1 : fl0;
-    if ((fh & F_TYPE) == T_LIQ && (fh & F_NEAR_OBST)) {
+    for (int i = 1; i < Q; ++i) {
+      const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
+      const bool yz = (cy == 1 && ylo) || (cy == -1 && yhi) || (cz == 1 && zlo) || (cz == -1 && zhi);
+      if (near0 && (yz || (cx == 1 && wl0) || (cx == -1 && wr0))) f[i].x = ST::ld1(A + opp(i) * P + c);
+      if (near1 && (yz || (cx == -1 && wr1))) f[i].y = ST::ld1(A + opp(i) * P + c + 1);
+    }
+  } else if (near0 || near1) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      if (!(h ? near1 : near0)) continue;
       float tv[Q];
-      Nbr nb;
-      nb.setup(g, xa + h, y, z);
-      pull_liquid<Q, ST>(A, P, d.flags, nb, (int)c + h, true, tv);
+      pull_near<Q, ST>(A, P, d.flags, g, xa + h, y, z, tv);
 #pragma unroll
       for (int i = 0; i < Q; ++i) Lanes<float2>::at(f[i], h) = tv[i] * S;
     }
@@ -223,11 +249,11 @@ __device__ __forceinline__ bool bulk_pair(const typename ST::T* __restrict__ A,
   return (liq0 && !(usq.x < (float)(1.0 / 3.0))) || (liq1 && !(usq.y < (float)(1.0 / 3.0)));
 }
 
-template <int Q, class ST>
-__global__ void __launch_bounds__(kBulkThreads, 3)
+template <int Q, class ST, int NS, int MINB>
+__global__ void __launch_bounds__(kBulkThreads, MINB)
     k_stream_collide_bulk(Dev d, Geom g, Phys p, int ntx) {
   using T = typename ST::T;
-  using RING = BulkRing<Q, ST>;
+  using RING = BulkRing<Q, ST, NS>;
   constexpr int D = RING::stages;
   constexpr float S = ST::kScaleF;
   extern __shared__ __align__(128) unsigned char smem[];
@@ -337,7 +363,8 @@ __global__ void __launch_bounds__(kBulkThreads, 3)
     const uint8_t fl0 = xa < g.nx ? f2.x : (uint8_t)T_GAS;
     const uint8_t fl1 = xa + 1 < g.nx ? f2.y : (uint8_t)T_GAS;
     bad |= bulk_pair<Q, ST>(A, B, reinterpret_cast<const T*>(stage), kBulkSeg, kBulkHalo + 2 * t,
-                            xa, tc.y, tc.z, tc.w, fl0, fl1, d, g, p, les);
+                            xa, tc.y, tc.z, tc.w, fl0, fl1, d, g, p, les,
+                            (tc.x == 0 && g.nx <= kBulkTX) ? 2 : 0);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
   }

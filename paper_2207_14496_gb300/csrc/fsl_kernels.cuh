@@ -809,6 +809,105 @@ __global__ void __launch_bounds__(128, MINB) k_stream_collide_seg(Dev d, Geom g,
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
 }
 
+// One liquid cell (x, y, z) per thread, from a warp covering 32 consecutive
+// cells of a row: one stored value loaded per direction straight from the
+// source cell x - c_i (any alignment; the warp's 32 loads of a direction are
+// contiguous), the collision in FP32 on one cell (collide_v<Q, float>, the
+// same bits as the two-cell variants), one store per direction.  With a
+// single value per direction live, a thread needs about half the registers
+// of the two-cell form, so twice the warps fit on an SM.  Returns whether
+// the cell is liquid and reached |u|^2 >= 1/3.
+template <int Q, class ST>
+__device__ __forceinline__ bool cell_update(const Dev& d, const Geom& g, const Phys& p, int x, int y,
+                                            int z) {
+  using T = typename ST::T;
+  constexpr float S = ST::kScaleF;
+  const int cur = d.ctrl->step & 1;
+  const T* __restrict__ A = (const T*)d.pdf[cur];
+  T* __restrict__ B = (T*)d.pdf[cur ^ 1];
+  const long long P = g.plane;
+  const int row = g.sx * (y + g.ny * z);
+  const bool in = x < g.nx;
+  const uint8_t fl = in ? d.flags[row + x] : (uint8_t)T_GAS;
+  const bool liq = (fl & F_TYPE) == T_LIQ;
+  const int xs = in ? x : 0;  // in-row address for the lanes past the row end
+  // neighbour rows and columns (a wall side maps to the cell itself: such
+  // cells are near-obstacle and take the bounce-back values below)
+  const int ym = y > 0 ? y - 1 : (g.periodic[1] ? g.ny - 1 : y);
+  const int yp = y < g.ny - 1 ? y + 1 : (g.periodic[1] ? 0 : y);
+  const int zm = z > 0 ? z - 1 : (g.periodic[2] ? g.nz - 1 : z);
+  const int zp = z < g.nz - 1 ? z + 1 : (g.periodic[2] ? 0 : z);
+  const int xm = xs > 0 ? xs - 1 : (g.periodic[0] ? g.nx - 1 : xs);
+  const int xq = xs < g.nx - 1 ? xs + 1 : (g.periodic[0] ? 0 : xs);
+  float f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
+    const int yy = cy == 0 ? y : (cy == 1 ? ym : yp);
+    const int zz = cz == 0 ? z : (cz == 1 ? zm : zp);
+    const int xx = cx == 0 ? xs : (cx == 1 ? xm : xq);
+    f[i] = ST::ld1((A + i * P) + g.sx * (yy + g.ny * zz) + xx);
+  }
+  if (liq && (fl & F_NEAR_OBST)) {
+    if (!g.has_obst && !g.free_slip) {
+      // domain walls only: the directions whose source lies beyond a wall
+      // take the cell's own f*_(opp i) (halfway bounce-back)
+      const bool xlo = !g.periodic[0] && x == 0, xhi = !g.periodic[0] && x == g.nx - 1;
+      const bool ylo = !g.periodic[1] && y == 0, yhi = !g.periodic[1] && y == g.ny - 1;
+      const bool zlo = !g.periodic[2] && z == 0, zhi = !g.periodic[2] && z == g.nz - 1;
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int cx = dir_c(i, 0), cy = dir_c(i, 1), cz = dir_c(i, 2);
+        const bool cross = (cx == 1 && xlo) || (cx == -1 && xhi) || (cy == 1 && ylo) ||
+                           (cy == -1 && yhi) || (cz == 1 && zlo) || (cz == -1 && zhi);
+        if (cross) f[i] = ST::ld1(A + opp(i) * P + row + x);
+      }
+    } else {
+      float t[Q];
+      pull_near<Q, ST>(A, P, d.flags, g, x, y, z, t);
+#pragma unroll
+      for (int i = 0; i < Q; ++i) f[i] = t[i] * S;
+    }
+  }
+  const bool tr = p.trt != 0;
+  const float lamE = p.f.lam_e, lamO = tr ? p.f.lam_o : p.f.omega;
+  const float pe = p.f.pre_e, po = tr ? p.f.pre_o : p.f.pre_e;
+  const float usq = collide_v<Q, float>(f, f, lamE, lamO, pe, po, p.f.g[0], p.f.g[1], p.f.g[2], S,
+                                        LesLp::of(p));
+  if (liq) {
+    T* out = B + row + x;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) ST::st1(out + i * P, f[i]);
+  }
+  return liq && !(usq < (float)(1.0 / 3.0));
+}
+
+// Bulk pass over the list of 64-cell row segments with liquid, one cell per
+// thread: persistent warps walk the halves (32 cells) of the listed segments
+// with a grid stride, the list entry of the next iteration loaded one
+// iteration ahead.
+template <int Q, class ST, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_stream_collide_c1(Dev d, Geom g, Phys p, int ntx) {
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const int nh = 2 * (int)ctrl->n_tiles;
+  const int lane = threadIdx.x & 31;
+  const int tw = gridDim.x * (blockDim.x >> 5);
+  int k = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  int seg = k < nh ? d.l_tiles[k >> 1] : 0;
+  bool bad = false;
+  while (k < nh) {
+    const int kn = k + tw;
+    const int segn = kn < nh ? d.l_tiles[kn >> 1] : 0;
+    const int x = (seg % ntx) * 64 + 32 * (k & 1) + lane;
+    const int row = seg / ntx;
+    bad |= cell_update<Q, ST>(d, g, p, x, row % g.ny, row / g.ny);
+    k = kn;
+    seg = segn;
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
+}
+
 // Bulk pass of the 16-bit storages with four cells per thread: the four
 // stored values of each direction arrive as one aligned 8-byte load and stay
 // packed (two 32-bit words) until the collision unpacks them; the values
@@ -2279,13 +2378,38 @@ struct Kernels {
   static int variant_of(const Geom& g) {
     constexpr bool half = sizeof(typename ST::T) == 2;
     if ((g.variant >= 1 && g.variant <= 4) || g.variant == 6 || g.variant == 8 || g.variant == 9 ||
-        g.variant == 10 || g.variant == 12 || g.variant == 13)
+        g.variant == 10 || g.variant == 12 || g.variant == 13 || g.variant == 14 || g.variant == 15)
       return g.variant;
-    if ((g.variant == 5 || g.variant == 7 || g.variant == 11) && half) return g.variant;
+    if ((g.variant == 5 || g.variant == 7 || g.variant == 11 || g.variant == 16) && half)
+      return g.variant;
     return 2;
   }
   // variants that walk the list of liquid tiles of 256 cells
-  static bool uses_tiles256(int v) { return v == 4 || v == 9 || v == 10 || v == 11; }
+  static bool uses_tiles256(int v) { return v == 4 || v == 9 || v == 10 || v == 11 || v == 16; }
+  // variants that walk the list of liquid segments of 64 cells
+  static bool uses_segments64(int v) { return v == 6 || (v >= 12 && v <= 15); }
+  // persistent TMA pipeline (one producer warp, four consumer warps) with NS
+  // stages and at least MINB blocks per SM
+  template <int NS, int MINB>
+  static cudaError_t launch_tma(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
+    static int grid = 0;
+    constexpr size_t smem = BulkRing<Q, ST, NS>::bytes;
+    if (grid == 0) {
+      cudaError_t e = cudaFuncSetAttribute(k_stream_collide_bulk<Q, ST, NS, MINB>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0, dev = 0, sms = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_bulk<Q, ST, NS, MINB>,
+                                                        kBulkThreads, smem);
+      if (e != cudaSuccess) return e;
+      cudaGetDevice(&dev);
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      grid = (per_sm > 0 ? per_sm : 1) * sms;
+    }
+    const int ntx = (g.nx + kBulkTX - 1) / kBulkTX;
+    k_stream_collide_bulk<Q, ST, NS, MINB><<<grid, kBulkThreads, smem, s>>>(d, g, p, ntx);
+    return cudaGetLastError();
+  }
   // persistent cp.async pipeline with S stages and at least MINB blocks per SM
   template <int S, int MINB>
   static cudaError_t launch_cpa(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
@@ -2315,7 +2439,7 @@ struct Kernels {
         k_tiles<kBulkTX><<<(unsigned)((ntiles + 255) / 256), 256, 0, s>>>(d, g, ntx);
         return cudaGetLastError();
       }
-      if (variant_of(g) == 6 || variant_of(g) == 12 || variant_of(g) == 13) {
+      if (uses_segments64(variant_of(g))) {
         const int ntx = (g.nx + kWarpTX - 1) / kWarpTX;
         const long long ntiles = (long long)ntx * g.ny * g.nz;
         k_tiles<kWarpTX><<<(unsigned)((ntiles + 255) / 256), 256, 0, s>>>(d, g, ntx);
@@ -2328,6 +2452,27 @@ struct Kernels {
     if constexpr (ST::kShift) {
       const int v = variant_of(g);
       constexpr bool half = sizeof(typename ST::T) == 2;
+      if (v == 16) {
+        if constexpr (half) return launch_tma<3, 4>(d, g, p, s);
+      }
+      if (v == 14 || v == 15) {
+        static int grid14 = 0, grid15 = 0;
+        int& grid = v == 14 ? grid14 : grid15;
+        if (grid == 0) {
+          int per_sm = 0, dev = 0, sms = 0;
+          cudaError_t e = v == 14
+              ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_c1<Q, ST, 8>, 128, 0)
+              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_c1<Q, ST, 6>, 128, 0);
+          if (e != cudaSuccess) return e;
+          cudaGetDevice(&dev);
+          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+          grid = (per_sm > 0 ? per_sm : 1) * sms;
+        }
+        const int ntx = (g.nx + kWarpTX - 1) / kWarpTX;
+        if (v == 14) k_stream_collide_c1<Q, ST, 8><<<grid, 128, 0, s>>>(d, g, p, ntx);
+        else k_stream_collide_c1<Q, ST, 6><<<grid, 128, 0, s>>>(d, g, p, ntx);
+        return cudaGetLastError();
+      }
       if (v == 12 || v == 13) {
         // persistent warps over the 64-cell segment list: as many blocks as fit
         static int grid12 = 0, grid13 = 0;
@@ -2356,24 +2501,8 @@ struct Kernels {
         if (v == 10) return launch_cpa<3, 2>(d, g, p, s);
       }
       if (v == 4) {
-        // persistent grid: as many CTAs as fit on the GPU (queried once)
-        static int grid = 0;
-        constexpr size_t smem = BulkRing<Q, ST>::bytes;
-        if (grid == 0) {
-          cudaError_t e = cudaFuncSetAttribute(k_stream_collide_bulk<Q, ST>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               (int)smem);
-          if (e != cudaSuccess) return e;
-          int per_sm = 0, dev = 0, sms = 0;
-          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stream_collide_bulk<Q, ST>,
-                                                            kBulkThreads, smem);
-          if (e != cudaSuccess) return e;
-          cudaGetDevice(&dev);
-          cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-          grid = (per_sm > 0 ? per_sm : 1) * sms;
-        }
-        const int ntx = (g.nx + kBulkTX - 1) / kBulkTX;
-        k_stream_collide_bulk<Q, ST><<<grid, kBulkThreads, smem, s>>>(d, g, p, ntx);
+        if constexpr (half) return launch_tma<4, 3>(d, g, p, s);
+        else return launch_tma<3, 3>(d, g, p, s);
       } else if (v == 6) {
         static int grid = 0;
         constexpr size_t smem = WarpRing<Q, ST>::bytes;
@@ -2435,11 +2564,7 @@ struct Kernels {
   static int launches(const Geom& g) {
     const int bub = g.bubbles ? 6 : 0;
     if constexpr (ST::kShift)
-      return ((uses_tiles256(variant_of(g)) || variant_of(g) == 6 || variant_of(g) == 12 ||
-               variant_of(g) == 13)
-                  ? 11
-                  : 10) +
-             bub;
+      return ((uses_tiles256(variant_of(g)) || uses_segments64(variant_of(g))) ? 11 : 10) + bub;
     return 10 + bub;
   }
   static const Launch* table() {

@@ -121,7 +121,8 @@ EXPORTED = ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "f
             "fsl_adjoint_backward", "fsl_adjoint_destroy")
 VARIANTS = {"default": 0, "pair": 1, "pair_r128": 2, "pair_r96": 3, "tma": 4, "quad64": 5,
             "warp_tma": 6, "pair_pipe": 7, "pair_r80": 8, "cpa": 9, "cpa_deep": 10,
-            "cpa_r96": 11, "seg": 12, "seg_r128": 13}
+            "cpa_r96": 11, "seg": 12, "seg_r128": 13,
+            "cell": 14, "cell_r80": 15, "tma_r96": 16}
 KERNEL_STREAM_COLLIDE = 1
 KERNEL_BULK_PASS = 2
 

@@ -10,8 +10,8 @@ from paper_2207_14496_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 VARIANTS = ["pair", "pair_r128", "pair_r96", "pair_r80", "tma", "quad64", "warp_tma", "pair_pipe",
-            "cpa", "cpa_deep", "cpa_r96", "seg", "seg_r128"]
-HALF_ONLY = ("quad64", "pair_pipe", "cpa_r96")
+            "cpa", "cpa_deep", "cpa_r96", "seg", "seg_r128", "cell", "cell_r80", "tma_r96"]
+HALF_ONLY = ("quad64", "pair_pipe", "cpa_r96", "tma_r96")
 
 
 def _cases():
