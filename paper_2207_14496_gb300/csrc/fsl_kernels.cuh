@@ -230,6 +230,22 @@ struct Nbr {
   // x - c_i, direction i; across free-slip walls (specular reflection) the
   // cell x - c_i with the crossed components removed, in the mirrored
   // direction.  -1 for a no-slip wall or an obstacle (halfway bounce-back).
+  // The same source as source() without looking at the cell types: -1 only
+  // for a no-slip wall (an obstacle source is recognised by its flag byte).
+  template <int Q>
+  __device__ __forceinline__ int geo_source(int i, int& dir) const {
+    int a = X[1 - dir_c(i, 0)], b = Y[1 - dir_c(i, 1)], c = Z[1 - dir_c(i, 2)];
+    const int crossed = (a < 0 ? 1 : 0) | (b < 0 ? 2 : 0) | (c < 0 ? 4 : 0);
+    dir = i;
+    if (crossed) {
+      if ((crossed & fs) != crossed) return -1;
+      if (a < 0) a = X[1];
+      if (b < 0) b = Y[1];
+      if (c < 0) c = Z[1];
+      dir = mirror_dir<Q>(i, crossed);
+    }
+    return a + sx * (b + ny * c);
+  }
   template <int Q>
   __device__ __forceinline__ int source(int i, const uint8_t* flags, int& dir) const {
     int a = X[1 - dir_c(i, 0)], b = Y[1 - dir_c(i, 1)], c = Z[1 - dir_c(i, 2)];
@@ -1274,15 +1290,27 @@ __global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(D
     const R drg = (R)(3.0 * pg - 1.0);
     R feg[Q];
     feq_all<Q, SH, R>(feg, rg, drg, utx, uty, utz, utsq);
-    int tn[Q], sn[Q];  // type and cell of each incoming PDF's source
+    // Source cell of each incoming PDF (-1 beyond a no-slip wall), then its
+    // flag byte, stored value and fill level: every load has a valid address
+    // whatever the type turns out to be, so they are all in flight at once
+    // and the type only selects among the values.
+    uint8_t fb[Q];
+    R nv[Q], phn[Q];
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       int di;
-      const int n = nb.source<Q>(i, d.flags, di);
-      const int t = type_at(d.flags, n);
+      const int n = nb.geo_source<Q>(i, di);
+      const int ns = n >= 0 ? n : c;
+      fb[i] = n >= 0 ? d.flags[ns] : (uint8_t)T_OBST;
+      nv[i] = ST::ldw(A + di * P + ns);
+      phn[i] = (R)d.phi[ns];
+    }
+    int tn[Q];  // type of each incoming PDF's source
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int t = fb[i] & F_TYPE;
       tn[i] = t;
-      sn[i] = n;
-      if (is_fluid(t)) fin[i] = ST::ldw(A + di * P + n);      /* neighbour or mirror image */
+      if (is_fluid(t)) fin[i] = nv[i];                         /* neighbour or mirror image */
       else if (t == T_OBST) fin[i] = own[opp(i)];             /* halfway bounce-back */
       else fin[i] = feg[i] + feg[opp(i)] - own[opp(i)];       /* anti-bounce-back from gas */
     }
@@ -1306,8 +1334,7 @@ __global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(D
       if (t == T_LIQ) {
         dd = both;
       } else {
-        const int n = sn[io];
-        const int clsn = d.flags[n] & (F_NF | F_NE);
+        const int clsn = fb[io] & (F_NF | F_NE);
         const R f_in = SH ? fin[io] + (R)wgt<Q>(io) : fin[io];
         const R f_out = SH ? own[i] + (R)wgt<Q>(i) : own[i];
         R br;
@@ -1315,7 +1342,7 @@ __global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(D
         else if (clsx == 0) br = (clsn == F_NF) ? f_in : (clsn == F_NE) ? -f_out : both;
         else if (clsx == F_NF) br = (clsn == F_NF) ? both : -f_out;
         else br = (clsn == F_NE) ? both : f_in;
-        dd = (R)0.5 * (phx + (R)d.phi[n]) * br;
+        dd = (R)0.5 * (phx + phn[io]) * br;
       }
       dm = dm_has ? dm + dd : dd;
       dm_has = true;
@@ -1622,14 +1649,14 @@ __device__ inline RC curvature_open(const Geom& g, const double* phi, int x, int
           }
         n[ax] = sum / (RC)32;
       }
+      // without a branch, so that the loads of all six stencils can be in
+      // flight at once
       const RC len = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
-      if (len < (RC)1e-12) {
-        nh[sgn][0] = nh[sgn][1] = nh[sgn][2] = (RC)0;
-      } else {
-        nh[sgn][0] = n[0] / len;
-        nh[sgn][1] = n[1] / len;
-        nh[sgn][2] = n[2] / len;
-      }
+      const bool tiny = len < (RC)1e-12;
+      const RC l = tiny ? (RC)1 : len;
+      nh[sgn][0] = tiny ? (RC)0 : n[0] / l;
+      nh[sgn][1] = tiny ? (RC)0 : n[1] / l;
+      nh[sgn][2] = tiny ? (RC)0 : n[2] / l;
     }
     const RC dd = (RC)0.5 * (nh[0][a] - nh[1][a]);
     div = (a == 0) ? (RC)0 + dd : div + dd;
@@ -1940,9 +1967,17 @@ __global__ void __launch_bounds__(256) k_excess_gather(Dev d, Geom g) {
 // Thuerey class of an interface cell from its stencil neighbours.
 template <int Q>
 __device__ inline uint8_t iface_class(const Geom& g, const uint8_t* flags, int x, int y, int z) {
+  Nbr nb;
+  nb.setup(g, x, y, z);
+  const int c = nb.in(0, 0, 0);
   bool has_liq = false, has_gas = false;
+  // every flag load has a valid address (the cell itself beyond a wall), so
+  // the q - 1 loads are in flight together
+#pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const int t = type_at(flags, nb_at(g, x, y, z, rc(i, 0), rc(i, 1), rc(i, 2)));
+    const int n = nb.at(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2));
+    const uint8_t b = flags[n >= 0 ? n : c];
+    const int t = n >= 0 ? (b & F_TYPE) : T_OBST;
     if (t == T_LIQ) has_liq = true;
     if (t == T_GAS) has_gas = true;
   }
@@ -1952,7 +1987,7 @@ __device__ inline uint8_t iface_class(const Geom& g, const uint8_t* flags, int x
 }
 
 template <int Q, class ST>
-__global__ void __launch_bounds__(128) k_classify(Dev d, Geom g, Phys p) {
+__global__ void __launch_bounds__(128, 4) k_classify(Dev d, Geom g, Phys p) {
   using R = typename ST::R;
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;

@@ -16,6 +16,10 @@ coalesce and which schemes go unstable.
 `batched_waves` runs the set of 320 small independent wave domains as one
 batch and as one launch per domain.
 
+`drop_impact_precision` runs the drop impact of Sec. 4.5 (the benchmark
+workload) in FP64, FP32, FP16 and BF16 storage and reports the total-mass
+drift, the cavity depth and the crown inner diameter of each against FP64.
+
 `gravity_wave` reproduces the standing gravity wave of Sec. 4.1 at the
 paper's resolutions (L in {200, 400, 800}, omega = 1.8, Re = 10, d = L/2,
 a0 = 0.01 L, D3Q19 SRT) for the five refilling schemes and evaluates the
@@ -353,6 +357,97 @@ def batched_waves(steps: int = 4000, n_geom: int = 64, precision: str = "fp16",
     return out
 
 
+def _half_crossing(v0, v1, z0):
+    """Position between cell centres z0 and z0 + 1 where a linear fill level
+    going from v0 to v1 passes 1/2."""
+    return z0 + (0.5 - v0) / (v1 - v0)
+
+
+def drop_observables(phi, pool: float, diameter: float):
+    """Cavity depth h_ca* and crown inner diameter d_cr* of the drop impact
+    (Sec. 4.5), both in units of the drop diameter, from the fill level phi
+    (nz, ny, nx) on the cross-section through the centre with normal x, on
+    the phi = 1/2 contour (cell k has its centre at k + 1/2).
+
+    h_ca: from the cavity bottom to the initial surface height `pool`: the
+    lowest point of the centre column above which the fill level drops below
+    1/2 (0 where the centre column is liquid up to the initial surface).
+    d_cr: the crown's inner diameter at the initial surface height: in the row
+    of cells just below that height, from the centre outwards along y, the
+    first crossing of 1/2 on each side (0 where the centre is liquid)."""
+    nz, ny, nx = phi.shape
+    sec = phi[:, :, nx // 2]                      # (z, y)
+    col = sec[:, ny // 2]
+    zc = np.arange(nz) + 0.5
+    h = 0.0
+    k = int(np.argmax(col < 0.5))                 # first cell from the floor below 1/2
+    if col[k] < 0.5 and k > 0:
+        bottom = _half_crossing(col[k - 1], col[k], zc[k - 1])
+        h = max(pool - bottom, 0.0)
+    # the row of cells just below the initial surface height (centre at
+    # pool - 1/2): the flat surface of the initial state sits on its top face
+    k0 = min(max(int(math.floor(pool - 0.5)), 0), nz - 1)
+    row = sec[k0]
+    d = 0.0
+    yc = ny // 2
+    if row[yc] < 0.5:
+        right = next((j for j in range(yc + 1, ny) if row[j] >= 0.5), None)
+        left = next((j for j in range(yc - 1, -1, -1) if row[j] >= 0.5), None)
+        if right is not None and left is not None:
+            yr = _half_crossing(row[right - 1], row[right], right - 1 + 0.5)
+            yl = _half_crossing(row[left], row[left + 1], left + 0.5)
+            d = yr - yl
+    return h / diameter, d / diameter
+
+
+def drop_impact_precision(precisions=("fp64", "fp32", "fp16", "bf16"), steps: int = 2000,
+                          every: int = 50, n: int = 256):
+    """Error of the 16/32-bit storages against the FP64 path on the drop
+    impact (Sec. 4.5 in shape, the benchmark workload): total-mass drift,
+    cavity depth h_ca* and crown inner diameter d_cr* every `every` steps
+    through the impact and the splash that follows.  Returns the traces and,
+    per storage, the largest deviation from FP64 of each observable."""
+    from . import fsl
+    f = n / 256.0
+    w = inputs.drop_impact() if n == 256 else inputs.drop_impact(
+        n=n, pool=int(round(96 * f)), diameter=40.0 * f, gap=30.0 * f)
+    pool = float(w["h_ref"])
+    D = 40.0 * f
+    out = dict(workload=w["name"], steps=steps, every=every, diameter=D, pool=pool,
+               speed=0.05, traces={})
+    for prec in precisions:
+        sim = fsl.Sim(w["params"], prec)
+        sim.init_workload(w)
+        m0 = sim.total_mass()
+        tr = dict(step=[], tstar=[], mass_drift=[], h_ca=[], d_cr=[])
+        t0 = time.time()
+        for k in range(0, steps + 1, every):
+            if k:
+                sim.step(every)
+            h, d = drop_observables(sim.phi(), pool, D)
+            tr["step"].append(k)
+            tr["tstar"].append(k * 0.05 / D)
+            tr["mass_drift"].append((sim.total_mass() - m0) / m0)
+            tr["h_ca"].append(h)
+            tr["d_cr"].append(d)
+        tr["status"] = list(sim.status())
+        tr["seconds"] = time.time() - t0
+        sim.close()
+        out["traces"][prec] = tr
+    ref = out["traces"].get("fp64")
+    if ref is not None:
+        out["error_vs_fp64"] = {}
+        for prec, tr in out["traces"].items():
+            if prec == "fp64":
+                continue
+            out["error_vs_fp64"][prec] = dict(
+                h_ca_max_abs=float(np.max(np.abs(np.array(tr["h_ca"]) - ref["h_ca"]))),
+                d_cr_max_abs=float(np.max(np.abs(np.array(tr["d_cr"]) - ref["d_cr"]))),
+                mass_drift_max_abs=float(np.max(np.abs(tr["mass_drift"]))),
+                fp64_mass_drift_max_abs=float(np.max(np.abs(ref["mass_drift"]))))
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--L", type=int, nargs="*", default=[200, 400, 800])
@@ -365,9 +460,22 @@ def main():
                     help="also run the Sec. 4.4 Taylor bubble at these tube diameters D")
     ap.add_argument("--bubbly", action="store_true",
                     help="also run the Sec. 4.6 bubbly plane Poiseuille flow")
+    ap.add_argument("--drop-precision", default=None, metavar="FILE",
+                    help="run the drop-impact precision study (FP32/FP16/BF16 against FP64) "
+                         "and write its JSON here")
+    ap.add_argument("--drop-steps", type=int, default=2000)
+    ap.add_argument("--drop-size", type=int, default=256)
     ap.add_argument("--batched", type=int, default=0,
                     help="also run the batched standing-wave set for this many steps")
     args = ap.parse_args()
+    if args.drop_precision:
+        r = drop_impact_precision(steps=args.drop_steps, n=args.drop_size)
+        with open(args.drop_precision, "w") as fh:
+            json.dump(r, fh, indent=1)
+        print(json.dumps(dict(workload=r["workload"], error_vs_fp64=r.get("error_vs_fp64"))),
+              flush=True)
+        if not args.L:
+            return
     if args.batched:
         print(json.dumps(batched_waves(steps=args.batched)), flush=True)
     if args.bubbly:

@@ -187,3 +187,62 @@ def test_fp32_tracks_fp64_cell_by_cell(fsl, case):
     fl = (ta == 1) | (ta == 2)
     err = np.abs(a.pdfs()[:, fl] - b.pdfs()[:, fl]).max()
     assert err < 2e-6, err
+
+
+def _case(case):
+    if case == "wave64":
+        return inputs.standing_wave(64)
+    if case == "wave_wide":
+        return inputs.standing_wave(600, ny=40, depth=20.0, amp=2.0, nu=0.02)
+    if case == "dam":
+        return inputs.dam_break(nx=100, ny=48, nz=4, width=24, height=24, g=2e-4, nu=5e-3)
+    if case == "drop":
+        return inputs.drop_impact(n=40, pool=14, diameter=12.0, gap=9.0, speed=0.05, sigma=2e-3,
+                                  g=1e-5, nu=5e-3, nxy=36)
+    w = inputs.dam_break(nx=90, ny=50, nz=1, width=20, height=30, g=2e-4, nu=2e-3)
+    w["params"]["periodic"] = (False, False, True)
+    w["params"]["free_slip"] = (True, True, False)
+    w["params"]["les_cs"] = 0.1
+    return w
+
+
+# half an ulp of the stored offset f_i - w_i, relative: FP16 keeps 10
+# explicit significand bits, BF16 7
+HALF_ULP = {"fp16": 2.0 ** -11, "bf16": 2.0 ** -8}
+
+
+@pytest.mark.parametrize("prec", ["fp16", "bf16"])
+@pytest.mark.parametrize("case", ["wave64", "wave_wide", "dam", "drop", "freeslip_les"])
+def test_half_storage_tracks_fp64_cell_by_cell(fsl, case, prec):
+    """16-bit offset storage against the FP64 path, PDF by PDF, after 20
+    steps on every geometry class.  Each step rounds every stored offset once
+    (half an ulp of at most the largest offset |f - w| of the FP64 state)
+    and the collision carries earlier errors forward with gain about one, so
+    after n steps no PDF may differ by more than n half-ulps of that offset;
+    an indexing or scaling slip gives errors of the size of the offsets
+    themselves.  Cell types must agree (no conversion threshold sits within
+    the rounding error in these runs); the total mass moves by at most the
+    same rounding summed over the q values of a cell."""
+    w = _case(case)
+    steps = 20
+    a = fsl.Sim(w["params"], "fp64")
+    b = fsl.Sim(w["params"], prec)
+    for s in (a, b):
+        s.init_workload(w)
+    m0 = a.total_mass()
+    for s in (a, b):
+        s.step(steps)
+    ta, tb = a.types(), b.types()
+    assert np.array_equal(ta, tb)
+    fl = (ta == 1) | (ta == 2)
+    _, wts = fsl.lattice_table(w["params"]["q"])
+    fa, fb = a.pdfs()[:, fl], b.pdfs()[:, fl]
+    off = np.abs(fa - wts[:, None]).max()
+    err = np.abs(fa - fb).max()
+    bound = steps * HALF_ULP[prec] * off
+    print(f"{case}/{prec}: max |f16 - f64| {err:.3e}, bound {bound:.3e} (max offset {off:.3e})")
+    assert err <= bound, (err, bound)
+    # every stored value of a fluid cell (density about one) rounds by at most
+    # half an ulp of the largest offset per step
+    q = w["params"]["q"]
+    assert abs(b.total_mass() - m0) / m0 <= steps * q * HALF_ULP[prec] * off

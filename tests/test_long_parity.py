@@ -1,0 +1,85 @@
+"""FP64 parity over the full step counts of the benchmark configurations:
+the CUDA path against the CPU oracle, cell types bit-exact and PDFs, fill
+levels and interface masses within 1e-12 relative at every checkpoint.
+
+    FSL_LONG_PARITY=1 python -m pytest tests/test_long_parity.py -m gpu -q
+
+These runs take tens of minutes of host time (the oracle runs its per-cell
+loops on every host core), so they are skipped unless FSL_LONG_PARITY is
+set; with FSL_LONG_PARITY_OUT=<dir> each case writes its per-checkpoint
+error record there as JSON.
+
+- dam break 512 x 256 x 16, D3Q19 TRT, 8000 steps, each refilling scheme
+  (a scheme that goes unstable must do so at the same step on both sides);
+- drop impact 256^3, D3Q27 TRT, surface tension, 500 steps (through the
+  impact near step 200);
+- standing wave 128 x 64 x 4, D3Q19 SRT, 1500 steps.
+"""
+import json
+import os
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_14496_gb300 import inputs
+from parity_util import compare_state, make_pair
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not os.environ.get("FSL_LONG_PARITY"),
+                                 reason="long parity runs: set FSL_LONG_PARITY=1")]
+
+
+def _run(fsl, name, w, steps, every):
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.time()
+    try:
+        sim, orc = make_pair(fsl, w)
+        rec = dict(case=name, steps=steps, every=every, oracle_threads=threads, checkpoints=[])
+        done = conv = 0
+        while done < steps and orc.unstable_step < 0:
+            k = min(every, steps - done)
+            for _ in range(k):
+                orc.step(1)
+                c = orc.last_counts()
+                conv += c[0] + c[1] + c[2]
+            sim.step(k)
+            done += k
+            st = compare_state(sim, orc, done, 1e-12, label=name)
+            st.update(step=done, conversions=conv)
+            rec["checkpoints"].append(st)
+        assert sim.step_count == orc.step_count
+        assert sim.status()[1] == orc.unstable_step
+        rec.update(unstable_step=int(orc.unstable_step), conversions=conv,
+                   seconds=time.time() - t0,
+                   max_pdf_err=max(c["max_pdf_err"] for c in rec["checkpoints"]),
+                   bitwise_pdf=all(c["bitwise_pdf"] for c in rec["checkpoints"]))
+        sim.close()
+    finally:
+        oracle.set_threads(1)
+    out = os.environ.get("FSL_LONG_PARITY_OUT")
+    if out:
+        os.makedirs(out, exist_ok=True)
+        with open(os.path.join(out, f"{name}.json"), "w") as fh:
+            json.dump(rec, fh, indent=1)
+    return rec
+
+
+@pytest.mark.parametrize("scheme", inputs.REFILL_SCHEMES)
+def test_dam_break_512_8000_steps(fsl, scheme):
+    w = inputs.dam_break(refill=scheme)
+    rec = _run(fsl, f"dam_break_512x256x16_{scheme}", w, 8000, 1000)
+    assert rec["conversions"] > 1000
+
+
+def test_drop_impact_256_500_steps(fsl):
+    w = inputs.drop_impact()
+    rec = _run(fsl, "drop_impact_256", w, 500, 100)
+    assert rec["conversions"] > 1000
+
+
+def test_standing_wave_128x64x4_1500_steps(fsl):
+    w = inputs.standing_wave(128, nz=4, depth=32.0, amp=1.28, ny=64)
+    rec = _run(fsl, "standing_wave_128x64x4", w, 1500, 250)
+    assert rec["conversions"] > 0
