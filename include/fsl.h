@@ -256,13 +256,14 @@ enum { FSL_KERNEL_STREAM_COLLIDE = 1, FSL_KERNEL_BULK_PASS = 2 };
 fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4);
 
 /* Total mass of a state held in caller-owned device arrays, for callers that
- * cannot allocate device memory when they need it (during a CUDA graph
- * capture, inside a host callback or another allocator, or under a fixed
- * device-memory budget).  The paper has no counterpart: this is a library
- * convenience.  It allocates nothing: its reduction scratch is a static
- * 16 KiB device array inside the library, shared by all calls; calls whose
- * kernels overlap on the GPU race on it.  The first call on each device
- * looks up that array (make it before any stream capture).
+ * cannot allocate device memory when they need it (inside a host callback or
+ * another allocator, under a fixed device-memory budget, or in a loop that
+ * must not let an allocation synchronise the device).  The paper has no
+ * counterpart: this is a library convenience.  It allocates nothing: its
+ * reduction scratch is a static 16 KiB device array inside the library,
+ * shared by all calls; calls whose kernels overlap on the GPU race on it.
+ * The first call on each device looks up that array and loads the entry
+ * point's kernels (make it before any stream capture).
  *   cfg: lattice, precision, nx/ny/nz (other fields ignored);
  *   d_pdf: device, q planes of nx*ny*nz stored values in the dense layout
  *     (x fastest, no row padding) and the storage of cfg->precision (FP64:
@@ -283,9 +284,14 @@ fsl_status fsl_total_mass_noalloc(const fsl_config* cfg, const void* d_pdf,
  * sizes and refilling schemes).  A batch groups existing handles, each with
  * its own configuration, workspace and state; fsl_batch_step advances every
  * member by nsteps with one CUDA-graph launch per chunk of steps on the
- * batch's stream.  Inside that graph each member's kernels form an
- * independent branch (a child graph per member, no edges between members),
- * so the GPU runs the domains side by side instead of one after another.
+ * batch's stream.  When every member stores 16- or 32-bit PDFs and none runs
+ * the bubble model, each kernel of a step is launched once for all members
+ * of a lattice and storage (up to 256 members per launch, one member per
+ * blockIdx.y; the member reads its pointers, geometry and parameters from a
+ * record in its own workspace), so a step of the whole batch costs about a
+ * dozen launches; otherwise each member's kernels form an independent branch
+ * (a child graph per member, no edges between members).  Either way the GPU
+ * runs the domains side by side instead of one after another.
  *   handles: host array of n >= 1 handles, all initialised (fsl_init_fill or
  *     fsl_load done) and bound to streams of one device; the batch keeps the
  *     pointers, not the array; the handles must outlive the batch;

@@ -53,6 +53,38 @@ def tune(sim, reps: int = 5, candidates=CANDIDATES) -> dict:
     return dict(variant=best, ms=ms)
 
 
+def tune_step(sim, candidates, steps: int = 20) -> dict:
+    """Time whole steps (CUDA events on the simulation's stream, graph
+    replay) with each candidate variant and keep the fastest: the interface
+    pass runs beside the bulk pass and competes with it for the SMs, so the
+    fastest bulk pass alone need not give the fastest step.  The state is
+    checkpointed first and restored at the end, so the tuning steps leave no
+    trace.  Returns
+    {"variant": name, "ms_step": {name: ms per step}}."""
+    import torch
+    if sim.precision == "fp64":
+        return dict(variant="default", ms_step={})
+    ck = sim.save()
+    ms = {}
+    for v in candidates:
+        if not _allowed(sim, v):
+            continue
+        sim.set_variant(v)
+        sim.step(2)  # capture the step graph outside the timing
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(sim.stream)
+        sim.step(steps)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        ms[v] = e0.elapsed_time(e1) / steps
+    best = min(ms, key=ms.get)
+    sim.set_variant(best)
+    sim.load(ck)
+    return dict(variant=best, ms_step=ms)
+
+
 def tune_batch(sims, reps: int = 5, cache_path: str | None = None) -> dict:
     """Tune one representative per (lattice, storage, shape) and apply the
     pick to all simulations of that kind.  With `cache_path`, picks found in

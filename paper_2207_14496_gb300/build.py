@@ -1,10 +1,13 @@
 """Build libfsl.so (the CUDA library behind include/fsl.h) for sm_103a.
 
 Each translation unit is compiled by nvcc in parallel and linked into one
-shared library inside the package (``_build/libfsl.so``).  The FP64 kernels
-are compiled with ``-fmad=false`` (no multiply-add contraction) so that their
-results follow the source's operation order bit for bit; the FP32 / 16-bit
-kernels keep contraction on.
+shared library inside the package (``_build/libfsl.so``).  Every unit is
+compiled with ``-fmad=false`` (no multiply-add contraction): the FP64 kernels
+then follow the source's operation order bit for bit, and a kernel body that
+is compiled into more than one kernel (the single-domain and the batched
+launch of a step kernel) gives the same bits in each, because the compiler
+cannot contract a multiply and an add differently in the two.  The hot
+16/32-bit collision spells out its fused multiply-adds explicitly.
 """
 from __future__ import annotations
 
@@ -20,10 +23,10 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfsl.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-UNITS = {"fsl_api.cu": [], "fsl_noalloc.cu": []}
+UNITS = {"fsl_api.cu": ["-fmad=false"], "fsl_noalloc.cu": ["-fmad=false"]}
 for _p in ("fp64", "fp32", "fp16", "bf16"):
     for _q in (19, 27):
-        UNITS[f"k_{_p}_q{_q}.cu"] = ["-fmad=false"] if _p == "fp64" else []
+        UNITS[f"k_{_p}_q{_q}.cu"] = ["-fmad=false"]
 
 
 def _nvcc() -> str:

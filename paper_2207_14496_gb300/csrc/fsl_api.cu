@@ -37,7 +37,7 @@ constexpr long long kPlaneSkew = 512;  // elements added to every PDF plane
 enum Region {
   R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST,
   R_LIF, R_LIF2, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_LTILES, R_CTRL, R_TRACE, R_RED,
-  R_BLAB, R_BNEW, R_BK, R_BKNEW, R_BV, R_BVSEEN, R_BP, R_BHAS, R_COUNT
+  R_BLAB, R_BNEW, R_BK, R_BKNEW, R_BV, R_BVSEEN, R_BP, R_BHAS, R_SELF, R_COUNT
 };
 
 bool valid_config(const fsl_config* c) {
@@ -147,6 +147,8 @@ void region_sizes(const fsl_config* c, const Geom& g, size_t* sz) {
   }
   sz[R_TRACE] = (size_t)kTraceCapacity * 3 * sizeof(double);
   sz[R_RED] = (size_t)(2 * kReduceBlocks + 16) * sizeof(double);
+  // the handle's own member record for batched launches
+  sz[R_SELF] = sizeof(Member);
 }
 
 size_t layout(const fsl_config* c, const Geom& g, size_t* off) {
@@ -972,6 +974,7 @@ fsl_status fsl_adjoint_destroy(fsl_adjoint* a) {
 // ------------------------------------------------------------------ batch
 struct fsl_batch {
   std::vector<fsl_handle*> hs;
+  bool batched = false;           // one launch per kernel for all members
   cudaStream_t stream = nullptr;  // graph launches
   cudaStream_t cap = nullptr;     // private stream, used only for captures
   std::vector<cudaEvent_t> ev;    // per member: its stream's queued work
@@ -988,9 +991,74 @@ void batch_drop_graphs(fsl_batch* b) {
   b->graphs.clear();
 }
 
+// Whether the batch can run as one launch per kernel and step for all its
+// members: 16/32-bit storages and no bubble model.
+bool batchable(const fsl_batch* b) {
+  for (const fsl_handle* h : b->hs)
+    if (storage_bytes(h->cfg.precision) == 8 || h->g.bubbles) return false;
+  return true;
+}
+
+// Each member's record (device pointers, geometry, parameters) into its own
+// workspace, where the batched kernels read it.
+fsl_status write_member_records(fsl_batch* b) {
+  for (fsl_handle* h : b->hs) {
+    const Member m = {h->d, h->g, h->p};
+    FSL_CK(cudaMemcpyAsync(h->base + h->off[R_SELF], &m, sizeof(Member), cudaMemcpyHostToDevice,
+                           b->stream));
+  }
+  FSL_CK(cudaStreamSynchronize(b->stream));
+  return FSL_OK;
+}
+
+// One graph of `steps` steps of the batch, one launch per kernel for the
+// members of each launch table (lattice and storage), at most kBatchMax
+// members per launch.
+fsl_status batch_capture_joint(fsl_batch* b, int steps, cudaGraphExec_t* out) {
+  fsl_status st = write_member_records(b);
+  if (st != FSL_OK) return st;
+  struct Group {
+    const Launch* L;
+    MemberTable t;
+    int n;
+    BatchGrid bg;
+  };
+  std::vector<Group> groups;
+  for (fsl_handle* h : b->hs) {
+    Group* gp = nullptr;
+    for (Group& q : groups)
+      if (q.L == h->L && q.n < kBatchMax) gp = &q;
+    if (!gp) {
+      groups.push_back(Group{h->L, {}, 0, {1}});
+      gp = &groups.back();
+    }
+    gp->t.m[gp->n++] = reinterpret_cast<const Member*>(h->base + h->off[R_SELF]);
+    const long long ntiles = (long long)((h->g.nx + 63) / 64) * h->g.ny * h->g.nz;
+    const int tb = (int)((ntiles + 255) / 256);
+    if (tb > gp->bg.tiles) gp->bg.tiles = tb;
+  }
+  cudaError_t e = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture (batch)");
+  cudaError_t le = cudaSuccess;
+  for (int k = 0; k < steps && le == cudaSuccess; ++k)
+    for (const Group& q : groups)
+      if (le == cudaSuccess) le = q.L->batch_step(q.t, q.n, q.bg, b->cap);
+  cudaGraph_t g;
+  e = cudaStreamEndCapture(b->cap, &g);
+  if (le != cudaSuccess || e != cudaSuccess) {
+    if (e == cudaSuccess) cudaGraphDestroy(g);
+    return cuda_fail(le != cudaSuccess ? le : e, "batch capture");
+  }
+  cudaError_t ie = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate (batch)");
+  return FSL_OK;
+}
+
 // one graph of `steps` steps of every member: a child graph per member, no
 // edges between them
 fsl_status batch_capture(fsl_batch* b, int steps, cudaGraphExec_t* out) {
+  if (b->batched) return batch_capture_joint(b, steps, out);
   cudaGraph_t parent;
   FSL_CK(cudaGraphCreate(&parent, 0));
   for (fsl_handle* h : b->hs) {
@@ -1056,6 +1124,7 @@ fsl_status fsl_batch_step(fsl_batch* b, int nsteps) {
   if (stale) {
     for (fsl_handle* h : b->hs)
       if (!h->ready) return FSL_ERR_STATE;
+    b->batched = batchable(b);
     batch_drop_graphs(b);
     b->gens.resize(n);
     for (size_t i = 0; i < n; ++i) b->gens[i] = b->hs[i]->gen;

@@ -95,8 +95,8 @@ struct BulkRing {
 // the list does not matter to its consumers).  Cells beyond the row's extent
 // hold the gas type.
 template <int TX>
-__global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
-  static_assert(TX % 32 == 0, "tiles of whole 32-cell rows pieces");
+__device__ __forceinline__ void tiles_body(const Dev& d, const Geom& g, int ntx) {
+  static_assert(TX % 32 == 0, "tiles of whole 32-cell row pieces");
   __shared__ int warp_n[8];
   __shared__ unsigned base;
   Ctrl* ctrl = d.ctrl;
@@ -136,6 +136,17 @@ __global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
   __syncthreads();
   if (liq) d.l_tiles[base + warp_n[warp] + __popc(m & ((1u << lane) - 1u))] = (int)k;
 }
+
+template <int TX>
+__global__ void __launch_bounds__(256) k_tiles(Dev d, Geom g, int ntx) {
+  tiles_body<TX>(d, g, ntx);
+}
+template <int TX>
+__global__ void __launch_bounds__(256) kb_tiles(MemberTable t) {
+  FSL_MEMBER(t);
+  tiles_body<TX>(d, g, (g.nx + TX - 1) / TX);
+}
+
 
 // Update of two neighbouring cells (xa, xa + 1) of row `row` = (y, z), read
 // from A and written to B, whose pulled values sit in a staged row segment:
@@ -255,7 +266,6 @@ __global__ void __launch_bounds__(kBulkThreads, MINB)
   using T = typename ST::T;
   using RING = BulkRing<Q, ST, NS>;
   constexpr int D = RING::stages;
-  constexpr float S = ST::kScaleF;
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + D * RING::stage_bytes);
   uint64_t* empty = full + D;

@@ -124,6 +124,25 @@ struct Dev {
   uint8_t* bhas;
 };
 
+// One member of a batch of independent domains, as the batched kernels read
+// it: a copy of the handle's device pointers, geometry and parameters kept in
+// the handle's own workspace (region written by the host before a capture).
+struct Member {
+  Dev d;
+  Geom g;
+  Phys p;
+};
+// Members of one batched launch, one per blockIdx.y (a kernel parameter).
+constexpr int kBatchMax = 256;
+struct MemberTable {
+  const Member* m[kBatchMax];
+};
+// Grid extent along x of each batched kernel, per member (the kernels' own
+// loops cover whatever cells, list entries or segments the member holds).
+struct BatchGrid {
+  int tiles;  // blocks of the segment-list pre-pass (largest member)
+};
+
 // Per-precision-family launch table, implemented in fsl_prec_*.cu.
 // Side stream and events of a handle: the interface pass of a step runs on
 // `side`, forked from and joined back to the step's stream, concurrently with
@@ -156,6 +175,8 @@ struct Launch {
   cudaError_t (*stream_collide)(const Dev&, const Geom&, const Phys&, cudaStream_t);
   // kernel launches of one step
   int (*launches_per_step)(const Geom&);
+  // one time step of n members (one launch per kernel for all of them)
+  cudaError_t (*batch_step)(const MemberTable& t, int n, const BatchGrid& bg, cudaStream_t);
 };
 
 // Launch tables, one translation unit per (storage, lattice).

@@ -1,8 +1,10 @@
 // FSLBM step kernels, templated on the lattice (Q = 19 | 27) and the PDF
 // storage (SF64 | SF32 | SF16 | SBF16).  Each precision family instantiates
-// them in its own translation unit (fsl_prec_*.cu); the FP64 unit is compiled
-// with -fmad=false so that its arithmetic is bit-reproducible against a plain
-// FP64 evaluation in the operation order written here.
+// them in its own translation unit (k_<storage>_q<Q>.cu).  Every unit is
+// compiled with -fmad=false: the FP64 arithmetic is then bit-reproducible
+// against a plain FP64 evaluation in the operation order written here, and a
+// body inlined into both the single-domain and the batched kernel gives the
+// same bits in each.
 //
 // One step (Sec. 2 and 3 of the paper), t -> t+1:
 //   k_stream_collide  (bulk variants) pull streaming (Eq. nm-lbm-streaming),
@@ -37,6 +39,17 @@ namespace fsl {
 // A physical parameter in the arithmetic type R: the FP64 value for the FP64
 // path, the copy rounded once on the host otherwise.
 #define PAR(R, p, name) (sizeof(R) == 8 ? (R)(p).name : (R)(p).f.name)
+
+// The member of a batched launch that this block serves (blockIdx.y), copied
+// into local values so that the body's stores cannot alias them.
+#define FSL_MEMBER(t)                          \
+  const Member& mb_ = *(t).m[blockIdx.y];      \
+  const Dev d = mb_.d;                         \
+  const Geom g = mb_.g;                        \
+  const Phys p = mb_.p;                        \
+  (void)d;                                     \
+  (void)g;                                     \
+  (void)p
 
 #define FSL_GRID_LOOP(k, n) \
   for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < (n); k += gridDim.x * blockDim.x)
@@ -803,8 +816,8 @@ __global__ void __launch_bounds__(BT, MINB) k_stream_collide_lp(Dev d, Geom g, P
 // of the next iteration is loaded one iteration ahead.  No gas-only warp is
 // launched and a warp's flag and PDF loads are in flight together, so every
 // segment costs one memory round trip.
-template <int Q, class ST, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_stream_collide_seg(Dev d, Geom g, Phys p, int ntx) {
+template <int Q, class ST>
+__device__ __forceinline__ void stream_collide_seg_body(const Dev& d, const Geom& g, const Phys& p, int ntx) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const int ntl = (int)ctrl->n_tiles;
@@ -824,6 +837,16 @@ __global__ void __launch_bounds__(128, MINB) k_stream_collide_seg(Dev d, Geom g,
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
 }
+template <int Q, class ST, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_stream_collide_seg(Dev d, Geom g, Phys p, int ntx) {
+  stream_collide_seg_body<Q, ST>(d, g, p, ntx);
+}
+template <int Q, class ST>
+__global__ void __launch_bounds__(128, 4) kb_stream_collide_seg(MemberTable t) {
+  FSL_MEMBER(t);
+  stream_collide_seg_body<Q, ST>(d, g, p, (g.nx + 63) / 64);
+}
+
 
 // One liquid cell (x, y, z) per thread, from a warp covering 32 consecutive
 // cells of a row: one stored value loaded per direction straight from the
@@ -1246,7 +1269,7 @@ __global__ void __launch_bounds__(128) k_stream_collide(Dev d, Geom g, Phys p) {
 // interface list of a 256^3 drop impact then fits in one wave: 90 us at
 // three blocks, 70 at four, and the step 2 % faster again at five)
 template <int Q, class ST>
-__global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(Dev d, Geom g, Phys p) {
+__device__ __forceinline__ void stream_collide_if_body(const Dev& d, const Geom& g, const Phys& p) {
   using T = typename ST::T;
   using R = typename ST::R;
   constexpr bool SH = ST::kShift;
@@ -1383,6 +1406,16 @@ __global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(D
   }
   if (bad) atomicCAS(&ctrl->unstable_step, -1, ctrl->step + 1);
 }
+template <int Q, class ST>
+__global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(Dev d, Geom g, Phys p) {
+  stream_collide_if_body<Q, ST>(d, g, p);
+}
+template <int Q, class ST>
+__global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) kb_stream_collide_if(MemberTable t) {
+  FSL_MEMBER(t);
+  stream_collide_if_body<Q, ST>(d, g, p);
+}
+
 
 // ------------------------------------------------------------ conversion
 
@@ -1394,7 +1427,7 @@ __global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) k_stream_collide_if(D
        k += (gridDim.x * blockDim.x) >> 5)
 
 template <int Q>
-__global__ void __launch_bounds__(256) k_fill(Dev d, Geom g) {
+__device__ __forceinline__ void fill_body(const Dev& d, const Geom& g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nif = ctrl->n_if, nfill = ctrl->n_fill;
@@ -1429,9 +1462,19 @@ __global__ void __launch_bounds__(256) k_fill(Dev d, Geom g) {
     warp_append(created, n, &ctrl->n_new, d.l_new);
   }
 }
+template <int Q>
+__global__ void __launch_bounds__(256) k_fill(Dev d, Geom g) {
+  fill_body<Q>(d, g);
+}
+template <int Q>
+__global__ void __launch_bounds__(256) kb_fill(MemberTable t) {
+  FSL_MEMBER(t);
+  fill_body<Q>(d, g);
+}
+
 
 template <int Q, class ST>
-__global__ void __launch_bounds__(256) k_empty(Dev d, Geom g) {
+__device__ __forceinline__ void empty_body(const Dev& d, const Geom& g) {
   using R = typename ST::R;
   constexpr bool SH = ST::kShift;
   Ctrl* ctrl = d.ctrl;
@@ -1469,8 +1512,18 @@ __global__ void __launch_bounds__(256) k_empty(Dev d, Geom g) {
     warp_append(won, n, &ctrl->n_l2i, d.l_l2i);
   }
 }
+template <int Q, class ST>
+__global__ void __launch_bounds__(256) k_empty(Dev d, Geom g) {
+  empty_body<Q, ST>(d, g);
+}
+template <int Q, class ST>
+__global__ void __launch_bounds__(256) kb_empty(MemberTable t) {
+  FSL_MEMBER(t);
+  empty_body<Q, ST>(d, g);
+}
 
-static __global__ void __launch_bounds__(256) k_finalise(Dev d) {
+
+__device__ __forceinline__ void finalise_body(const Dev& d) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nf = ctrl->n_fill, ne = ctrl->n_empty;
@@ -1492,6 +1545,12 @@ static __global__ void __launch_bounds__(256) k_finalise(Dev d) {
     }
   }
 }
+static __global__ void __launch_bounds__(256) k_finalise(Dev d) { finalise_body(d); }
+static __global__ void __launch_bounds__(256) kb_finalise(MemberTable t) {
+  FSL_MEMBER(t);
+  finalise_body(d);
+}
+
 
 // ------------------------------------------------------------ normals
 // Parker-Youngs gradient of phi at cell (x, y, z): per axis a, the centred
@@ -1745,7 +1804,7 @@ __device__ __forceinline__ bool valid_src(const uint8_t* flags, int n) {
 // neighbours run in direction order (shuffled to every lane), so the FP64
 // result equals a sequential evaluation in that order.
 template <int Q, class ST>
-__global__ void __launch_bounds__(128) k_refill(Dev d, Geom g, Phys p) {
+__device__ __forceinline__ void refill_body(const Dev& d, const Geom& g, const Phys& p) {
   using T = typename ST::T;
   using R = typename ST::R;
   constexpr bool SH = ST::kShift;
@@ -1893,10 +1952,20 @@ __global__ void __launch_bounds__(128) k_refill(Dev d, Geom g, Phys p) {
     if (lane == 0) d.rho[c] = SH ? 1.0 + (double)r : (double)r;
   }
 }
+template <int Q, class ST>
+__global__ void __launch_bounds__(128) k_refill(Dev d, Geom g, Phys p) {
+  refill_body<Q, ST>(d, g, p);
+}
+template <int Q, class ST>
+__global__ void __launch_bounds__(128) kb_refill(MemberTable t) {
+  FSL_MEMBER(t);
+  refill_body<Q, ST>(d, g, p);
+}
+
 
 // ------------------------------------------------------------ excess mass
 template <int Q>
-__global__ void __launch_bounds__(256) k_excess_share(Dev d, Geom g) {
+__device__ __forceinline__ void excess_share_body(const Dev& d, const Geom& g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nf = ctrl->n_fill, ne = ctrl->n_empty;
@@ -1929,11 +1998,21 @@ __global__ void __launch_bounds__(256) k_excess_share(Dev d, Geom g) {
     }
   }
 }
+template <int Q>
+__global__ void __launch_bounds__(256) k_excess_share(Dev d, Geom g) {
+  excess_share_body<Q>(d, g);
+}
+template <int Q>
+__global__ void __launch_bounds__(256) kb_excess_share(MemberTable t) {
+  FSL_MEMBER(t);
+  excess_share_body<Q>(d, g);
+}
+
 
 // Each receiver gathers the shares of its converted neighbours, summed in
 // direction order.
 template <int Q>
-__global__ void __launch_bounds__(256) k_excess_gather(Dev d, Geom g) {
+__device__ __forceinline__ void excess_gather_body(const Dev& d, const Geom& g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nr = ctrl->n_recv;
@@ -1962,6 +2041,16 @@ __global__ void __launch_bounds__(256) k_excess_gather(Dev d, Geom g) {
     }
   }
 }
+template <int Q>
+__global__ void __launch_bounds__(256) k_excess_gather(Dev d, Geom g) {
+  excess_gather_body<Q>(d, g);
+}
+template <int Q>
+__global__ void __launch_bounds__(256) kb_excess_gather(MemberTable t) {
+  FSL_MEMBER(t);
+  excess_gather_body<Q>(d, g);
+}
+
 
 // ------------------------------------------------------------ classes / curvature
 // Thuerey class of an interface cell from its stencil neighbours.
@@ -1987,7 +2076,7 @@ __device__ inline uint8_t iface_class(const Geom& g, const uint8_t* flags, int x
 }
 
 template <int Q, class ST>
-__global__ void __launch_bounds__(128, 4) k_classify(Dev d, Geom g, Phys p) {
+__device__ __forceinline__ void classify_body(const Dev& d, const Geom& g, const Phys& p) {
   using R = typename ST::R;
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
@@ -2015,6 +2104,16 @@ __global__ void __launch_bounds__(128, 4) k_classify(Dev d, Geom g, Phys p) {
     warp_append(is_if, c, &ctrl->n_if_next, lnext);
   }
 }
+template <int Q, class ST>
+__global__ void __launch_bounds__(128, 4) k_classify(Dev d, Geom g, Phys p) {
+  classify_body<Q, ST>(d, g, p);
+}
+template <int Q, class ST>
+__global__ void __launch_bounds__(128, 4) kb_classify(MemberTable t) {
+  FSL_MEMBER(t);
+  classify_body<Q, ST>(d, g, p);
+}
+
 
 // The interface list of the current step from the flags (initial state, state
 // loaded from a checkpoint).
@@ -2062,7 +2161,7 @@ __device__ inline int block_max(int v, int* sh) {
 // fixed tree order); the last block to finish combines the partials in block
 // order and advances the counters.
 constexpr int kEndBlocks = 64;
-static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
+__device__ __forceinline__ void end_step_body(const Dev& d, const Geom& g) {
   __shared__ double shd[256];
   __shared__ int shi[256];
   __shared__ bool last;
@@ -2146,6 +2245,12 @@ static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) {
     ctrl->step += 1;
   }
 }
+static __global__ void __launch_bounds__(256) k_end_step(Dev d, Geom g) { end_step_body(d, g); }
+static __global__ void __launch_bounds__(256) kb_end_step(MemberTable t) {
+  FSL_MEMBER(t);
+  end_step_body(d, g);
+}
+
 
 // ------------------------------------------------------------ initialisation
 static __global__ void k_ctrl_reset(Ctrl* ctrl, int trace_every) {
@@ -2420,7 +2525,9 @@ struct Kernels {
     return 2;
   }
   // variants that walk the list of liquid tiles of 256 cells
-  static bool uses_tiles256(int v) { return v == 4 || v == 9 || v == 10 || v == 11 || v == 16; }
+  static bool uses_tiles256(int v) {
+    return v == 4 || v == 9 || v == 10 || v == 11 || v == 16;
+  }
   // variants that walk the list of liquid segments of 64 cells
   static bool uses_segments64(int v) { return v == 6 || (v >= 12 && v <= 15); }
   // persistent TMA pipeline (one producer warp, four consumer warps) with NS
@@ -2602,9 +2709,34 @@ struct Kernels {
       return ((uses_tiles256(variant_of(g)) || uses_segments64(variant_of(g))) ? 11 : 10) + bub;
     return 10 + bub;
   }
+  // One step of n members of this lattice and storage, each kernel launched
+  // once for all of them (blockIdx.y = member).  The bulk pass is the
+  // segment-list kernel whatever variant a member selected (all variants give
+  // the same bits).  16/32-bit storages only; FP64 batches step their members
+  // one by one.
+  static cudaError_t batch_step(const MemberTable& t, int n, const BatchGrid& bg, cudaStream_t s) {
+    if constexpr (ST::kShift) {
+      const unsigned m = (unsigned)n;
+      kb_stream_collide_if<Q, ST><<<dim3(16, m), 128, 0, s>>>(t);
+      kb_tiles<kWarpTX><<<dim3((unsigned)bg.tiles, m), 256, 0, s>>>(t);
+      kb_stream_collide_seg<Q, ST><<<dim3(32, m), 128, 0, s>>>(t);
+      kb_fill<Q><<<dim3(4, m), 256, 0, s>>>(t);
+      kb_empty<Q, ST><<<dim3(4, m), 256, 0, s>>>(t);
+      kb_finalise<<<dim3(4, m), 256, 0, s>>>(t);
+      kb_refill<Q, ST><<<dim3(8, m), 128, 0, s>>>(t);
+      kb_excess_share<Q><<<dim3(4, m), 256, 0, s>>>(t);
+      kb_excess_gather<Q><<<dim3(4, m), 256, 0, s>>>(t);
+      kb_classify<Q, ST><<<dim3(16, m), 128, 0, s>>>(t);
+      kb_end_step<<<dim3(kEndBlocks, m), 256, 0, s>>>(t);
+      return cudaGetLastError();
+    } else {
+      (void)t; (void)n; (void)bg; (void)s;
+      return cudaErrorNotSupported;
+    }
+  }
   static const Launch* table() {
     static const Launch L = {&step, &init, &total_mass, &max_velocity, &export_pdf,
-                             &pre_bulk, &stream_collide, &launches};
+                             &pre_bulk, &stream_collide, &launches, &batch_step};
     return &L;
   }
 };

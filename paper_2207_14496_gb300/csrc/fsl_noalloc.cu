@@ -1,19 +1,20 @@
 // Allocation-free total mass of a state held in caller-owned device arrays.
 //
 // Some callers cannot allocate device memory at the point where they need this
-// observable: code that runs while a CUDA graph is being captured (a
-// cudaMalloc there is not allowed in the capture), code inside a host callback
-// or inside another allocator's bookkeeping, or a process whose device memory
-// budget is fixed up front.  This entry point therefore takes its reduction
-// scratch (one partial sum per block) from a file-scope static device array
-// instead of a workspace.  The array is modest (kMaxBlocks doubles, 16 KiB)
-// and every GPU that loads the library keeps it until the process exits.
+// observable: code inside a host callback or inside another allocator's
+// bookkeeping, a process whose device-memory budget is fixed up front, or a
+// loop that must not let a cudaMalloc synchronise the device.  This entry
+// point therefore takes its reduction scratch (one partial sum per block)
+// from a file-scope static device array instead of a workspace.  The array is
+// modest (kMaxBlocks doubles, 16 KiB) and every GPU that loads the library
+// keeps it until the process exits.
 //
 // The first call on each device looks up the array's device address (with
-// that device current) and caches it; make that first call before any stream
-// capture.  All calls share the array: each call overwrites the partials it
-// uses (nothing has to start at zero), and calls whose kernels overlap on the
-// GPU (different streams without ordering) race on it.
+// that device current), caches it, and loads every kernel this entry point
+// can launch, so that later calls load nothing; make that first call before
+// any stream capture.  All calls share the array: each call overwrites the
+// partials it uses (nothing has to start at zero), and calls whose kernels
+// overlap on the GPU (different streams without ordering) race on it.
 #include <cstdint>
 #include <mutex>
 
@@ -38,8 +39,10 @@ static __device__ __align__(256) double g_mass_partials[kMaxBlocks];
 std::mutex g_mu;
 void* g_scratch[kMaxDevices] = {};
 
+cudaError_t load_kernels();
+
 // Device address of the scratch on the current device, looked up once per
-// device (with that device current).
+// device (with that device current), together with loading the kernels.
 cudaError_t scratch_on_current_device(double** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -49,6 +52,8 @@ cudaError_t scratch_on_current_device(double** out) {
   if (!g_scratch[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_mass_partials);
+    if (e != cudaSuccess) return e;
+    e = load_kernels();
     if (e != cudaSuccess) return e;
     g_scratch[dev] = p;
   }
@@ -106,17 +111,36 @@ __global__ void __launch_bounds__(kThreads) k_mass_dense_final(const double* par
   if (threadIdx.x == 0) *out = sh[0];
 }
 
+// Launch errors are read with cudaPeekAtLastError, which leaves an error of
+// unrelated earlier work in place for its owner (it is reported here too).
 template <int Q, class ST>
 cudaError_t launch(const void* pdf, const uint8_t* types, const double* mass, const double* lost,
                    long long n, double* scratch, double* out, cudaStream_t s) {
   const int nb = (int)((n + kCellsPerBlock - 1) / kCellsPerBlock);
   k_mass_dense_partial<Q, ST><<<nb, kThreads, 0, s>>>(
       static_cast<const typename ST::T*>(pdf), types, mass, lost, n, scratch);
+  cudaError_t e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return e;
   k_mass_dense_final<<<1, kThreads, 0, s>>>(scratch, nb, out);
-  return cudaGetLastError();
+  return cudaPeekAtLastError();
 }
 
-thread_local char g_msg[160];
+// Loads the module code of every kernel above on the current device (with
+// lazy module loading a kernel is otherwise loaded at its first launch).
+cudaError_t load_kernels() {
+  const void* fns[] = {
+      (const void*)k_mass_dense_partial<19, SF64>,  (const void*)k_mass_dense_partial<27, SF64>,
+      (const void*)k_mass_dense_partial<19, SF32>,  (const void*)k_mass_dense_partial<27, SF32>,
+      (const void*)k_mass_dense_partial<19, SF16>,  (const void*)k_mass_dense_partial<27, SF16>,
+      (const void*)k_mass_dense_partial<19, SBF16>, (const void*)k_mass_dense_partial<27, SBF16>,
+      (const void*)k_mass_dense_final};
+  for (const void* f : fns) {
+    cudaFuncAttributes a;
+    const cudaError_t e = cudaFuncGetAttributes(&a, f);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
 
 }  // namespace
 

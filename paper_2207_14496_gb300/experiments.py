@@ -286,10 +286,10 @@ def batched_waves(steps: int = 4000, n_geom: int = 64, precision: str = "fp16",
     width 1..8, depth L/2, amplitude 0.01 L, viscosity U[1e-3, 1e-2],
     g = 1e-5) times the five refilling schemes, FP16 storage.  Runs `steps`
     steps (a) with one fsl_step per domain, one after another on a single
-    stream (the per-domain baseline) and (b) as one batch (one graph launch
-    per `chunk` steps, the domains as independent branches) after the
-    variant autotuner; reports both throughputs (all cells) and checks that
-    every domain ends bit-identical in the two runs."""
+    stream (the per-domain baseline, after the variant autotuner) and (b) as
+    one batch (one graph launch per `chunk` steps, each kernel of a step
+    launched once for all domains); reports both throughputs (all cells) and
+    checks that sampled domains end bit-identical in the two runs."""
     import torch
 
     from . import autotune, fsl

@@ -105,3 +105,56 @@ def test_batch_with_bubble_model_matches_individual_runs(fsl, prec):
         assert np.array_equal(solo[i][5], st[5]), f"member {i}: bubble labels differ"
         assert np.array_equal(solo[i][6], st[6]), f"member {i}: pressures differ"
     b.close()
+
+
+def test_batch_fp16_members_track_fp64(fsl):
+    """FP16 members of a batch (one launch per kernel for all of them) against
+    the FP64 path, PDF by PDF after 20 steps: within 20 half-ulps of FP16
+    (2^-11) of the largest offset |f - w|, cell types equal."""
+    ws = _members()
+    sims = []
+    for w in ws:
+        s = fsl.Sim(w["params"], "fp16")
+        s.init_workload(w)
+        sims.append(s)
+    b = fsl.Batch(sims, chunk=8)
+    b.step(20)
+    _, wts = fsl.lattice_table(19)
+    for i, w in enumerate(ws):
+        r = fsl.Sim(w["params"], "fp64")
+        r.init_workload(w)
+        r.step(20)
+        t = r.types()
+        assert np.array_equal(t, sims[i].types()), i
+        fl = (t == 1) | (t == 2)
+        fa, fb = r.pdfs()[:, fl], sims[i].pdfs()[:, fl]
+        off = np.abs(fa - wts[:, None]).max()
+        assert np.abs(fa - fb).max() <= 20 * 2.0 ** -11 * off, i
+        r.close()
+    b.close()
+
+
+def test_batch_of_many_members_and_two_lattices(fsl):
+    """More members than one launch takes (256), of two lattices: every
+    member equals its solo run bit for bit."""
+    ws = []
+    for k in range(300):
+        q = 27 if k % 7 == 0 else 19
+        ws.append(inputs.standing_wave(16 + 2 * (k % 5), nz=1 + k % 2, q=q,
+                                       refill=inputs.REFILL_SCHEMES[k % 5]))
+    sims = []
+    for w in ws:
+        s = fsl.Sim(w["params"], "fp16")
+        s.init_workload(w)
+        sims.append(s)
+    b = fsl.Batch(sims, chunk=16)
+    b.step(16)
+    for i in range(0, 300, 23):
+        r = fsl.Sim(ws[i]["params"], "fp16")
+        r.init_workload(ws[i])
+        r.step(16)
+        _same(_state(r), _state(sims[i]), f"member {i}")
+        r.close()
+    b.close()
+    for s in sims:
+        s.close()
