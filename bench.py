@@ -54,10 +54,10 @@ KERNEL_OF = {"pair": "k_stream_collide_lp", "pair_r128": "k_stream_collide_lp",
              "seg_r128": "k_stream_collide_seg", "cell": "k_stream_collide_c1",
              "cell_r80": "k_stream_collide_c1", "tma_r96": "k_stream_collide_bulk"}
 
-# FP64 ALU peak for the bit-exact path, which is built without multiply-add
-# contraction (one FP64 instruction per operation): 152 SMs x 2 FP64 lanes
-# per SM per clock x 2.07 GHz (= 1.26 TFLOP/s when counted as FMA flops).
-FP64_PEAK_TFLOPS = 152 * 2 * 2.07e9 / 1e12
+# FP64 instruction peak for the bit-exact path (built without multiply-add
+# contraction): the part's nominal 1.25 TFLOP/s of FP64 counts an FMA as two
+# flops, so its FP64 pipes retire 0.625 T FP64 instructions per second.
+FP64_PEAK_TINSTR = 1.25 / 2
 # nominal HBM3e bandwidth of the part, for the second roofline fraction
 NOMINAL_HBM_GBS = 7900.0
 
@@ -129,13 +129,14 @@ def replica_mlups(cells: int, steps: int, ms_max: float, world: int) -> float:
     return world * cells * steps / (ms_max * 1e-3) / 1e6
 
 
-def time_precision(fsl, w, precision, steps, warmup, dev, barrier, start=0, pre_impact=0):
+def time_precision(fsl, w, precision, steps, warmup, dev, barrier, start=0, pre_impact=0,
+                   variant=None):
     """Device-resident timing: CUDA events on the library's stream around K
     steps (captured CUDA graphs), after W warm-up steps.  The state is first
     advanced `start` steps (untimed) so that the timed window lies in the
-    phase after the drop has hit the pool; with pre_impact > 0 the same
-    number of steps is also timed from step W (before the impact) and
-    reported beside it."""
+    phase after the drop has hit the pool; with pre_impact > 0 that many
+    steps are also timed from step W + 3, before the impact (replayed from a
+    checkpoint with the tuned variant), and reported beside it."""
     import torch
 
     from paper_2207_14496_gb300 import autotune
@@ -143,19 +144,11 @@ def time_precision(fsl, w, precision, steps, warmup, dev, barrier, start=0, pre_
     sim = fsl.Sim(w["params"], precision, device=dev)
     sim.init_workload(w)
     sim.set_trace(1)
-    early = None
+    early_state = None
     if pre_impact > 0:
+        # the state before the impact, replayed with the tuned variant below
         sim.step(warmup)
-        torch.cuda.synchronize(dev)
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(sim.stream)
-        sim.step(pre_impact)
-        a1.record(sim.stream)
-        torch.cuda.synchronize(dev)
-        t_ms = a0.elapsed_time(a1)
-        early = dict(from_step=warmup, steps=pre_impact, ms_per_step=t_ms / pre_impact,
-                     mlups=sim.N * pre_impact / (t_ms * 1e-3) / 1e6)
+        early_state = sim.save()
     done = sim.step_count
     if start > done:
         sim.step(start - done)
@@ -163,7 +156,13 @@ def time_precision(fsl, w, precision, steps, warmup, dev, barrier, start=0, pre_
     torch.cuda.synchronize(dev)
     # bulk-pass variant picked by the autotuner on the warmed-up state (untimed;
     # the measurement leaves the state unchanged)
-    tuned = autotune.tune(sim, reps=5)
+    if variant and precision != "fp64":
+        # a fixed bulk-pass variant (profiling runs, where the timings that
+        # the autotuner would compare are distorted)
+        sim.set_variant(variant)
+        tuned = dict(variant=variant, ms={})
+    else:
+        tuned = autotune.tune(sim, reps=5)
     # then whole steps with the three fastest bulk passes (the interface pass
     # runs beside the bulk pass and competes with it)
     if tuned["ms"]:
@@ -190,6 +189,20 @@ def time_precision(fsl, w, precision, steps, warmup, dev, barrier, start=0, pre_
     status = sim.status()
     launches = sim.launches_per_step() * steps
     first = sim.step_count - steps
+    early = None
+    if early_state is not None:
+        sim.load(early_state)
+        sim.step(3)  # the step graph is captured again after the load
+        torch.cuda.synchronize(dev)
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(sim.stream)
+        sim.step(pre_impact)
+        a1.record(sim.stream)
+        torch.cuda.synchronize(dev)
+        t_ms = a0.elapsed_time(a1)
+        early = dict(from_step=warmup + 3, steps=pre_impact, ms_per_step=t_ms / pre_impact,
+                     mlups=sim.N * pre_impact / (t_ms * 1e-3) / 1e6, variant=tuned["variant"])
     del sim
     torch.cuda.empty_cache()
     return dict(ms=ms, ms_per_step=ms / steps, mlups=n_cells * steps / (ms * 1e-3) / 1e6,
@@ -326,6 +339,9 @@ def main():
     ap.add_argument("--pre-impact", type=int, default=100,
                     help="steps also timed from step W, before the impact, for the headline "
                          "storage (0: skip)")
+    ap.add_argument("--variant", default=None,
+                    help="bulk-pass variant of the 16/32-bit storages instead of the autotuner's "
+                         "pick (for profiling captures)")
     ap.add_argument("--size", type=int, default=256,
                     help="edge of the drop-impact cube (256 = the benchmark workload; smaller "
                          "sizes scale pool and drop, for profiling captures)")
@@ -371,7 +387,8 @@ def main():
         if p == "fp64":
             k = args.fp64_steps or max(10, args.steps // 5)
         res[p] = time_precision(fsl, w, p, k, args.warmup, local, barrier, start=args.start,
-                                pre_impact=args.pre_impact if p == precs[0] else 0)
+                                pre_impact=args.pre_impact if p == precs[0] else 0,
+                                variant=args.variant)
         res[p]["steps"] = k
     head = precs[0]
     h = res[head]
@@ -386,14 +403,15 @@ def main():
 
     def roofline(r, prec):
         if prec == "fp64":
-            # FP64 is bound by the FP64 pipe on GB300: algorithmic flops of the
-            # stream-collide kernel (D3Q27 TRT with Guo forcing, counted per
-            # liquid cell) over its launch time
-            flops = r["n_liquid"] * FLOPS_PER_CELL_D3Q27_TRT
-            ach = flops / (r["kernel_ms"] * 1e-3) / 1e12
-            return dict(bound="alu", achieved=ach, peak=FP64_PEAK_TFLOPS, unit="TFLOP/s",
-                        frac=ach / FP64_PEAK_TFLOPS, traffic=None, kernel="k_stream_collide",
-                        peak_source="152 SMs x 2 FP64 lanes/clk x 2.07 GHz, one op per instruction")
+            # FP64 is bound by the FP64 pipe on GB300: FP64 instructions of the
+            # stream-collide kernel (D3Q27 TRT with Guo forcing, per liquid
+            # cell, counted by ncu) over its launch time
+            instr = r["n_liquid"] * FP64_INSTR_PER_LIQUID_CELL_D3Q27_TRT
+            ach = instr / (r["kernel_ms"] * 1e-3) / 1e12
+            return dict(bound="alu", achieved=ach, peak=FP64_PEAK_TINSTR,
+                        unit="T FP64 instructions/s", frac=ach / FP64_PEAK_TINSTR, traffic=None,
+                        kernel="k_stream_collide",
+                        peak_source="nominal 1.25 TFLOP/s FP64 (an FMA counted as two flops)")
         ach = r["kernel_bytes"] / (r["kernel_ms"] * 1e-3) / 1e9
         return dict(bound="hbm", achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
                     frac=ach / peaks["hbm_gbs"], frac_nominal=ach / NOMINAL_HBM_GBS,
@@ -450,16 +468,19 @@ def main():
         dist.destroy_process_group()
 
 
-# FP64 operations per liquid-cell update of the stream-collide kernel for
-# D3Q27 TRT with Guo forcing (adds, multiplies, divides as written in the
-# kernel source, each shared subexpression counted once).
-FLOPS_PER_CELL_D3Q27_TRT = 1060
+# FP64 instructions per liquid-cell update of the FP64 stream-collide kernel
+# for D3Q27 TRT with Guo forcing: ncu's smsp__sass_thread_inst_executed_op_
+# fp64_pred_on.sum (1.3365e9) over the liquid cells (1.526e6) of one launch
+# on the 160^3 drop impact.
+FP64_INSTR_PER_LIQUID_CELL_D3Q27_TRT = 876
 # DRAM bytes (read + write) per launch of the bulk kernel on the 256^3
 # workload, from one single-pass ncu capture of the autotuner's launches of
 # each variant, with the digest of the kernel sources the capture ran
 # (kernel_source_digest); an entry whose digest differs from the sources
 # built now is stale and reported as null.
-TRAFFIC = {}
+TRAFFIC = {("fp16", "tma"): (673.29e6, "692712fcc4df4e0e"),
+           ("fp16", "tma_r96"): (686.29e6, "692712fcc4df4e0e"),
+           ("fp32", "tma"): (1370.99e6, "692712fcc4df4e0e")}
 KERNEL_SOURCES = ("fsl_kernels.cuh", "fsl_bulk.cuh", "fsl_lattice.cuh", "fsl_internal.h")
 
 

@@ -67,7 +67,7 @@ def _run(fsl, name, w, steps, every):
     return rec
 
 
-@pytest.mark.parametrize("les", [False, True])
+@pytest.mark.parametrize("les", [False, True], ids=["plain", "les"])
 @pytest.mark.parametrize("scheme", inputs.REFILL_SCHEMES)
 def test_dam_break_512_8000_steps(fsl, scheme, les):
     """As configured (TRT, nu = 5e-4, no turbulence model) the column's
