@@ -35,13 +35,15 @@ struct Ctrl {
   int trace_every;     // 0: no trace
   int trace_count;     // records written (ring index = count % capacity)
   unsigned timeout;    // error bits: 1 CAS retry cap, 2 refill without source, 4 copy wait gave up,
-                       // 8 bubble union retry cap
+                       // 8 bubble union retry cap, 16 grid barrier wait gave up
   unsigned n_emptied;  // to-gas cells actually converted this step
   unsigned end_blocks; // end-of-step blocks finished
   unsigned n_tiles;    // tiles holding liquid cells, listed this step (16/32-bit path)
   unsigned n_if_next;  // interface cells of the next step (appended by k_classify)
   unsigned tile_next;  // next tile handed out by the dynamically scheduled bulk kernel
   unsigned tile_done;  // blocks of that kernel finished (the last one resets both)
+  unsigned bar;        // block arrivals at the grid barriers of the conversion kernel
+                       // (reset by the end-of-step kernel)
 };
 
 constexpr int kTraceCapacity = 1 << 16;

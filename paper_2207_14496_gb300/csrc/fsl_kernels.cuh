@@ -19,14 +19,17 @@
 //                     fill level m/rho (Eq. nm-fslbm-mass), conversion marks
 //                     (threshold eps_phi) and warp-ballot compaction of the
 //                     to-liquid and to-gas cells;
-//   k_fill            commit fill levels; gas neighbours of filled cells become
+//   k_convert         one cooperative launch of five phases separated by
+//                     grid-wide barriers (the batched path launches them one
+//                     by one):
+//     fill            commit fill levels; gas neighbours of filled cells become
 //                     new interface cells; to-gas neighbours are kept (filling
 //                     wins a conflict);
-//   k_empty           liquid neighbours of emptied cells become interface;
-//   k_finalise        excess mass (Eq. nm-fslbm-excess-mass), type change;
-//   k_refill          EQ, EQ+NEQ, GEQ, EXT, AVG refilling (Sec. 3.1);
-//   k_excess_share    share per receiver, receiver compaction;
-//   k_excess_gather   receivers gather their shares in direction order;
+//     empty           liquid neighbours of emptied cells become interface;
+//     finalise/share  type change, excess mass (Eq. nm-fslbm-excess-mass) and
+//                     its share per receiver, receiver compaction;
+//     refill          EQ, EQ+NEQ, GEQ, EXT, AVG refilling (Sec. 3.1);
+//     excess gather   receivers gather their shares in direction order;
 //   k_classify        Thuerey classes and curvature K = -div(n_hat) for the
 //                     next step, clean-up of the per-step marks, and the next
 //                     step's interface list (two lists, by step parity);
@@ -1421,10 +1424,16 @@ __global__ void __launch_bounds__(128, ST::kShift ? 5 : 1) kb_stream_collide_if(
 
 
 // lane i of a warp examines direction i of the warp's cell (warp-per-cell
-// loops); lanes >= Q stay idle but take part in the ballots
+// loops); lanes >= Q stay idle but take part in the ballots.  Consecutive
+// items go to consecutive blocks, so that a short list is spread over all SMs
+// (its FP64 arithmetic shares each SM's two FP64 lanes with few other items).
 #define FSL_WARP_PER_ITEM(k, n)                                                     \
-  for (unsigned k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < (n);          \
+  for (unsigned k = (threadIdx.x >> 5) * gridDim.x + blockIdx.x; k < (n);           \
        k += (gridDim.x * blockDim.x) >> 5)
+// one thread per item, spread over the blocks in the same way
+#define FSL_SPREAD_LOOP(k, n)                                                       \
+  for (unsigned k = threadIdx.x * gridDim.x + blockIdx.x; k < (n);                  \
+       k += gridDim.x * blockDim.x)
 
 template <int Q>
 __device__ __forceinline__ void fill_body(const Dev& d, const Geom& g) {
@@ -1461,10 +1470,6 @@ __device__ __forceinline__ void fill_body(const Dev& d, const Geom& g) {
     }
     warp_append(created, n, &ctrl->n_new, d.l_new);
   }
-}
-template <int Q>
-__global__ void __launch_bounds__(256) k_fill(Dev d, Geom g) {
-  fill_body<Q>(d, g);
 }
 template <int Q>
 __global__ void __launch_bounds__(256) kb_fill(MemberTable t) {
@@ -1513,42 +1518,79 @@ __device__ __forceinline__ void empty_body(const Dev& d, const Geom& g) {
   }
 }
 template <int Q, class ST>
-__global__ void __launch_bounds__(256) k_empty(Dev d, Geom g) {
-  empty_body<Q, ST>(d, g);
-}
-template <int Q, class ST>
 __global__ void __launch_bounds__(256) kb_empty(MemberTable t) {
   FSL_MEMBER(t);
   empty_body<Q, ST>(d, g);
 }
 
 
-__device__ __forceinline__ void finalise_body(const Dev& d) {
+// Type of cell c once this step's conversions are applied: a cell marked to
+// fill becomes liquid, a cell still marked to empty becomes gas (every marked
+// cell is on the fill or the empty list, and the marks of earlier steps were
+// cleared by k_classify).  Beyond a wall: T_OBST.
+__device__ __forceinline__ int final_type(const uint8_t* flags, int c) {
+  if (c < 0) return T_OBST;
+  const uint8_t b = flags[c];
+  return (b & F_TO_LIQ) ? T_LIQ : (b & F_TO_GAS) ? T_GAS : (b & F_TYPE);
+}
+
+// Conversion of the filled and emptied cells with the share of their excess
+// mass per receiver (Eq. nm-fslbm-excess-mass), one warp per cell: lane 0
+// changes the type and computes the excess mass, lanes 1..Q-1 test the
+// neighbour x + c_i, which receives a share when it is an interface cell after
+// the conversions (its final type, read from its marks, so that the answer
+// does not depend on whether its own conversion was written yet), and claim
+// it for the receiver list.  Receivers are counted per direction.
+template <int Q>
+__device__ __forceinline__ void finalise_share_body(const Dev& d, const Geom& g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nf = ctrl->n_fill, ne = ctrl->n_empty;
-  FSL_GRID_LOOP(k, nf + ne) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  FSL_WARP_PER_ITEM(k, nf + ne) {
     const bool fill = k < nf;
     const int c = fill ? d.l_fill[k] : d.l_empty[k - nf];
     const uint8_t fl = d.flags[c];
-    if (fill) {
-      d.mex[c] = (d.phi[c] - 1.0) * d.rho[c];
-      d.flags[c] = (uint8_t)((fl & ~F_TYPE) | T_LIQ);
-      d.phi[c] = 1.0;
-      d.mass[c] = d.rho[c];
-    } else if (fl & F_TO_GAS) {
-      d.mex[c] = d.phi[c] * d.rho[c];
-      d.flags[c] = (uint8_t)((fl & ~F_TYPE) | T_GAS);
-      d.phi[c] = 0.0;
-      d.mass[c] = 0.0;
-      atomicAdd(&ctrl->n_emptied, 1u);
+    if (!fill && !(fl & F_TO_GAS)) continue;  // kept by a filling neighbour (warp-uniform)
+    int x, y, z;
+    cell_xyz(g, c, x, y, z);
+    int n = -1;
+    bool recv = false, claimed = false;
+    if (lane >= 1 && lane < Q) {
+      n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
+      recv = final_type(d.flags, n) == T_IF;
+      if (recv) claimed = byte_or(d.claim, n, 1) == 0;
+    }
+    const int nr = __popc(__ballot_sync(FULL, recv));
+    warp_append(claimed, n, &ctrl->n_recv, d.l_recv);
+    if (lane == 0) {
+      double mex;
+      if (fill) {
+        mex = (d.phi[c] - 1.0) * d.rho[c];
+        d.flags[c] = (uint8_t)((fl & ~F_TYPE) | T_LIQ);
+        d.phi[c] = 1.0;
+        d.mass[c] = d.rho[c];
+      } else {
+        mex = d.phi[c] * d.rho[c];
+        d.flags[c] = (uint8_t)((fl & ~F_TYPE) | T_GAS);
+        d.phi[c] = 0.0;
+        d.mass[c] = 0.0;
+        atomicAdd(&ctrl->n_emptied, 1u);
+      }
+      if (nr == 0) {
+        d.lost[c] += mex;
+        d.mex[c] = 0.0;
+      } else {
+        d.mex[c] = mex / (double)nr;
+      }
     }
   }
 }
-static __global__ void __launch_bounds__(256) k_finalise(Dev d) { finalise_body(d); }
-static __global__ void __launch_bounds__(256) kb_finalise(MemberTable t) {
+template <int Q>
+__global__ void __launch_bounds__(256) kb_finalise_share(MemberTable t) {
   FSL_MEMBER(t);
-  finalise_body(d);
+  finalise_share_body<Q>(d, g);
 }
 
 
@@ -1816,10 +1858,8 @@ __device__ __forceinline__ void refill_body(const Dev& d, const Geom& g, const P
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const unsigned nn = ctrl->n_new;
-  const unsigned wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const unsigned nw = (gridDim.x * blockDim.x) >> 5;
   const int scheme = p.refill;
-  for (unsigned k = wid; k < nn; k += nw) {
+  FSL_WARP_PER_ITEM(k, nn) {
     const int c = d.l_new[k];
     int x, y, z;
     cell_xyz(g, c, x, y, z);
@@ -1953,10 +1993,6 @@ __device__ __forceinline__ void refill_body(const Dev& d, const Geom& g, const P
   }
 }
 template <int Q, class ST>
-__global__ void __launch_bounds__(128) k_refill(Dev d, Geom g, Phys p) {
-  refill_body<Q, ST>(d, g, p);
-}
-template <int Q, class ST>
 __global__ void __launch_bounds__(128) kb_refill(MemberTable t) {
   FSL_MEMBER(t);
   refill_body<Q, ST>(d, g, p);
@@ -1964,90 +2000,92 @@ __global__ void __launch_bounds__(128) kb_refill(MemberTable t) {
 
 
 // ------------------------------------------------------------ excess mass
-template <int Q>
-__device__ __forceinline__ void excess_share_body(const Dev& d, const Geom& g) {
-  Ctrl* ctrl = d.ctrl;
-  if (frozen(ctrl)) return;
-  const unsigned nf = ctrl->n_fill, ne = ctrl->n_empty;
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  FSL_WARP_PER_ITEM(k, nf + ne) {
-    const bool fill = k < nf;
-    const int c = fill ? d.l_fill[k] : d.l_empty[k - nf];
-    if (!fill && !(d.flags[c] & F_TO_GAS)) continue;  // not converted (warp-uniform)
-    int x, y, z;
-    cell_xyz(g, c, x, y, z);
-    int n = -1;
-    bool recv = false, claimed = false;
-    if (lane >= 1 && lane < Q) {
-      n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
-      recv = type_at(d.flags, n) == T_IF;
-      if (recv) claimed = byte_or(d.claim, n, 1) == 0;
-    }
-    // receivers counted per direction (with multiplicity)
-    const int nr = __popc(__ballot_sync(FULL, recv));
-    warp_append(claimed, n, &ctrl->n_recv, d.l_recv);
-    if (lane == 0) {
-      const double mex = d.mex[c];
-      if (nr == 0) {
-        d.lost[c] += mex;
-        d.mex[c] = 0.0;
-      } else {
-        d.mex[c] = mex / (double)nr;
-      }
-    }
-  }
-}
-template <int Q>
-__global__ void __launch_bounds__(256) k_excess_share(Dev d, Geom g) {
-  excess_share_body<Q>(d, g);
-}
-template <int Q>
-__global__ void __launch_bounds__(256) kb_excess_share(MemberTable t) {
-  FSL_MEMBER(t);
-  excess_share_body<Q>(d, g);
-}
-
-
 // Each receiver gathers the shares of its converted neighbours, summed in
-// direction order.
+// direction order; one thread per receiver (its flag loads, then its share
+// loads, in flight together).
 template <int Q>
 __device__ __forceinline__ void excess_gather_body(const Dev& d, const Geom& g) {
   Ctrl* ctrl = d.ctrl;
   if (frozen(ctrl)) return;
   const unsigned nr = ctrl->n_recv;
-  const unsigned FULL = 0xffffffffu;
-  const int lane = threadIdx.x & 31;
-  FSL_WARP_PER_ITEM(k, nr) {
+  FSL_SPREAD_LOOP(k, nr) {
     const int r = d.l_recv[k];
     int x, y, z;
     cell_xyz(g, r, x, y, z);
-    double v = 0.0;
-    bool conv = false;
-    if (lane >= 1 && lane < Q) {
-      const int n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
-      conv = n >= 0 && (d.flags[n] & (F_TO_LIQ | F_TO_GAS));
-      if (conv) v = d.mex[n];
+    Nbr nb;
+    nb.setup(g, x, y, z);
+    int ns[Q];
+    uint8_t fb[Q];
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      ns[i] = nb.at(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2));
+      fb[i] = ns[i] >= 0 ? d.flags[ns[i]] : (uint8_t)0;
     }
-    const unsigned cm = __ballot_sync(FULL, conv);
     double sum = 0.0;
-    for (int j = 1; j < Q; ++j) {
-      const double vj = __shfl_sync(FULL, v, j);
-      if ((cm >> j) & 1u) sum += vj;
-    }
-    if (lane == 0) {
-      d.mass[r] = d.mass[r] + sum;
-      d.phi[r] = d.mass[r] / d.rho[r];
-    }
+#pragma unroll
+    for (int i = 1; i < Q; ++i)
+      if (fb[i] & (F_TO_LIQ | F_TO_GAS)) sum += d.mex[ns[i]];
+    d.mass[r] = d.mass[r] + sum;
+    d.phi[r] = d.mass[r] / d.rho[r];
   }
-}
-template <int Q>
-__global__ void __launch_bounds__(256) k_excess_gather(Dev d, Geom g) {
-  excess_gather_body<Q>(d, g);
 }
 template <int Q>
 __global__ void __launch_bounds__(256) kb_excess_gather(MemberTable t) {
   FSL_MEMBER(t);
+  excess_gather_body<Q>(d, g);
+}
+
+
+// ------------------------------------------------------------ conversion phase
+// Fill, empty, finalise with excess share, refill and excess gather of one
+// step in one cooperative launch (all blocks resident).  Each phase reads what the
+// previous phases wrote anywhere in the domain, so a grid-wide barrier
+// separates them: block arrivals are counted in ctrl->bar (phase k waits for
+// k * gridDim.x arrivals), the waits are bounded in time, and a block whose
+// wait gives up sets timeout bit 16 and leaves (the blocks still waiting then
+// give up in their turn).  The phases run the same bodies as the separate
+// kernels of the batched path, in the same order, so the results are the same.
+constexpr unsigned long long kBarrierWaitNs = 200000000ull;  // 0.2 s
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned target) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's writes before its arrival
+    atomicAdd(&ctrl->bar, 1u);
+    int good = 1;
+    const unsigned long long t0 = global_ns();
+    while (*(volatile unsigned*)&ctrl->bar < target) {
+      if (global_ns() - t0 > kBarrierWaitNs) {
+        atomicOr(&ctrl->timeout, 16u);
+        good = 0;
+        break;
+      }
+      __nanosleep(32);
+    }
+    __threadfence();  // the other blocks' writes before this block's reads
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+template <int Q, class ST>
+__global__ void __launch_bounds__(256) k_convert(Dev d, Geom g, Phys p) {
+  Ctrl* ctrl = d.ctrl;
+  if (frozen(ctrl)) return;
+  const unsigned nb = gridDim.x;
+  fill_body<Q>(d, g);
+  if (!grid_barrier(ctrl, nb)) return;
+  empty_body<Q, ST>(d, g);
+  if (!grid_barrier(ctrl, 2 * nb)) return;
+  finalise_share_body<Q>(d, g);
+  if (!grid_barrier(ctrl, 3 * nb)) return;
+  refill_body<Q, ST>(d, g, p);
+  if (!grid_barrier(ctrl, 4 * nb)) return;
   excess_gather_body<Q>(d, g);
 }
 
@@ -2241,6 +2279,7 @@ __device__ __forceinline__ void end_step_body(const Dev& d, const Geom& g) {
     ctrl->n_emptied = 0;
     ctrl->end_blocks = 0;
     ctrl->n_tiles = 0;
+    ctrl->bar = 0;
     __threadfence();
     ctrl->step += 1;
   }
@@ -2471,12 +2510,8 @@ struct Kernels {
     if (e == cudaSuccess) e = stream_collide(d, g, p, s);
     if (e == cudaSuccess && aux.side) e = cudaStreamWaitEvent(s, aux.join, 0);
     if (e != cudaSuccess) return e;
-    k_fill<Q><<<kListBlocks, 256, 0, s>>>(d, g);
-    k_empty<Q, ST><<<kListBlocks, 256, 0, s>>>(d, g);
-    k_finalise<<<kListBlocks, 256, 0, s>>>(d);
-    k_refill<Q, ST><<<kListBlocks, 128, 0, s>>>(d, g, p);
-    k_excess_share<Q><<<kListBlocks, 256, 0, s>>>(d, g);
-    k_excess_gather<Q><<<kListBlocks, 256, 0, s>>>(d, g);
+    e = convert(d, g, p, s);
+    if (e != cudaSuccess) return e;
     if (g.bubbles) {
       e = bubble_update<Q>(d, g, p, 0, s);
       if (e != cudaSuccess) return e;
@@ -2484,6 +2519,32 @@ struct Kernels {
     k_classify<Q, ST><<<kCellListBlocks, 128, 0, s>>>(d, g, p);
     k_end_step<<<kEndBlocks, 256, 0, s>>>(d, g);
     return cudaGetLastError();
+  }
+  // the conversion phase (k_convert), cooperative: at most four blocks per SM,
+  // as many as fit
+  static cudaError_t convert(const Dev& d, const Geom& g, const Phys& p, cudaStream_t s) {
+    static int grid = 0;
+    if (grid == 0) {
+      int per_sm = 0, dev = 0, sms = 0;
+      cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_convert<Q, ST>, 256, 0);
+      if (e != cudaSuccess) return e;
+      e = cudaGetDevice(&dev);
+      if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) return e;
+      if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+      grid = (per_sm < 4 ? per_sm : 4) * sms;
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_convert<Q, ST>, d, g, p);
   }
   static cudaError_t init(const Dev& d, const Geom& g, const Phys& p, int cur, const double* u0,
                           int have_obst, double h_ref, cudaStream_t s) {
@@ -2701,13 +2762,13 @@ struct Kernels {
     return cudaGetLastError();
   }
   // kernels of one step: interface pass, bulk pass (plus the tile list of
-  // the TMA variants), fill, empty, finalise, refill, excess share, excess
-  // gather, classify, end of step; six more with the bubble model
+  // the list-driven variants), conversion phase, classify, end of step; six
+  // more with the bubble model
   static int launches(const Geom& g) {
     const int bub = g.bubbles ? 6 : 0;
     if constexpr (ST::kShift)
-      return ((uses_tiles256(variant_of(g)) || uses_segments64(variant_of(g))) ? 11 : 10) + bub;
-    return 10 + bub;
+      return ((uses_tiles256(variant_of(g)) || uses_segments64(variant_of(g))) ? 6 : 5) + bub;
+    return 5 + bub;
   }
   // One step of n members of this lattice and storage, each kernel launched
   // once for all of them (blockIdx.y = member).  The bulk pass is the
@@ -2722,9 +2783,8 @@ struct Kernels {
       kb_stream_collide_seg<Q, ST><<<dim3(32, m), 128, 0, s>>>(t);
       kb_fill<Q><<<dim3(4, m), 256, 0, s>>>(t);
       kb_empty<Q, ST><<<dim3(4, m), 256, 0, s>>>(t);
-      kb_finalise<<<dim3(4, m), 256, 0, s>>>(t);
+      kb_finalise_share<Q><<<dim3(4, m), 256, 0, s>>>(t);
       kb_refill<Q, ST><<<dim3(8, m), 128, 0, s>>>(t);
-      kb_excess_share<Q><<<dim3(4, m), 256, 0, s>>>(t);
       kb_excess_gather<Q><<<dim3(4, m), 256, 0, s>>>(t);
       kb_classify<Q, ST><<<dim3(16, m), 128, 0, s>>>(t);
       kb_end_step<<<dim3(kEndBlocks, m), 256, 0, s>>>(t);
