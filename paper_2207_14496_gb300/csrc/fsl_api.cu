@@ -35,7 +35,7 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr long long kPlaneSkew = 512;  // elements added to every PDF plane
 
 enum Region {
-  R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST,
+  R_PDF0, R_PDF1, R_FLAGS, R_CLAIM, R_PHI, R_PHINEW, R_MASS, R_RHO, R_KAPPA, R_MEX, R_LOST, R_PHIF,
   R_LIF, R_LIF2, R_LFILL, R_LEMPTY, R_LNEW, R_LL2I, R_LRECV, R_LTILES, R_CTRL, R_TRACE, R_RED,
   R_BLAB, R_BNEW, R_BK, R_BKNEW, R_BV, R_BVSEEN, R_BP, R_BHAS, R_SELF, R_COUNT
 };
@@ -135,6 +135,8 @@ void region_sizes(const fsl_config* c, const Geom& g, size_t* sz) {
   sz[R_FLAGS] = sz[R_CLAIM] = cells;
   sz[R_PHI] = sz[R_PHINEW] = sz[R_MASS] = sz[R_RHO] = sz[R_KAPPA] = sz[R_MEX] = sz[R_LOST] =
       cells * sizeof(double);
+  // the FP32 copy of the fill level that the 16/32-bit kernels read
+  sz[R_PHIF] = c->precision == FSL_FP64 ? 0 : cells * sizeof(float);
   for (int r = R_LIF; r <= R_LRECV; ++r) sz[r] = cells * sizeof(int);
   // tile lists of the shared-memory variants: up to one entry per 64 cells of a row
   sz[R_LTILES] = (size_t)((g.nx + 63) / 64) * g.ny * g.nz * sizeof(int);
@@ -318,6 +320,7 @@ fsl_status fsl_create(const fsl_config* cfg, void* d_workspace, size_t bytes, vo
   d.claim = reinterpret_cast<uint8_t*>(base + h->off[R_CLAIM]);
   d.phi = reinterpret_cast<double*>(base + h->off[R_PHI]);
   d.phinew = reinterpret_cast<double*>(base + h->off[R_PHINEW]);
+  d.phif = cfg->precision == FSL_FP64 ? nullptr : reinterpret_cast<float*>(base + h->off[R_PHIF]);
   d.mass = reinterpret_cast<double*>(base + h->off[R_MASS]);
   d.rho = reinterpret_cast<double*>(base + h->off[R_RHO]);
   d.kappa = reinterpret_cast<double*>(base + h->off[R_KAPPA]);
@@ -665,6 +668,7 @@ fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
   c.n_if = c.n_fill = c.n_empty = c.n_new = c.n_l2i = c.n_recv = 0;
   c.n_emptied = c.end_blocks = c.n_tiles = 0;
   c.tile_next = c.tile_done = 0;
+  c.bar = 0;
   c.trace_every = h->trace_every;
   c.trace_count = 0;
   c.n_if_next = 0;
@@ -673,6 +677,11 @@ fsl_status fsl_load(fsl_handle* h, const void* host_src, size_t bytes) {
   // the interface list of the loaded step, from the loaded flags
   k_list_interface<<<4 * 152, 256, 0, h->stream>>>(h->d, h->g);
   FSL_CK(cudaGetLastError());
+  // the FP32 copy of the loaded fill levels
+  if (h->d.phif) {
+    k_phif_from_phi<<<4 * 152, 256, 0, h->stream>>>(h->d, h->g);
+    FSL_CK(cudaGetLastError());
+  }
   FSL_CK(cudaStreamSynchronize(h->stream));
   h->ready = true;
   return FSL_OK;

@@ -95,6 +95,7 @@ struct Dev {
   uint8_t* flags;
   uint8_t* claim;     // receiver claim bytes (zero between steps)
   double* phi;        // fill level
+  float* phif;        // FP32 copy of phi, written with it (16/32-bit path; null in FP64)
   double* phinew;     // fill level computed by stream-collide (interface cells)
   double* mass;       // cell mass (interface cells)
   double* rho;        // density recorded this step (interface cells)

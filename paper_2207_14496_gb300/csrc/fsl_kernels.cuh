@@ -43,6 +43,20 @@ namespace fsl {
 // path, the copy rounded once on the host otherwise.
 #define PAR(R, p, name) (sizeof(R) == 8 ? (R)(p).name : (R)(p).f.name)
 
+// Fill level of cell c written together with its FP32 copy (16/32-bit path),
+// so that the kernels that read many fill levels per cell in FP32 (interface
+// pass, normals, curvature) load 4-byte values and convert none of them.
+__device__ __forceinline__ void put_phi(const Dev& d, long long c, double v) {
+  d.phi[c] = v;
+  if (d.phif) d.phif[c] = (float)v;
+}
+// the fill levels in the working precision R: the FP32 copy for R = float
+template <class R>
+__device__ __forceinline__ const R* phi_work(const Dev& d) {
+  if constexpr (sizeof(R) == 4) return d.phif;
+  else return d.phi;
+}
+
 // The member of a batched launch that this block serves (blockIdx.y), copied
 // into local values so that the body's stores cannot alias them.
 #define FSL_MEMBER(t)                          \
@@ -1329,7 +1343,7 @@ __device__ __forceinline__ void stream_collide_if_body(const Dev& d, const Geom&
       const int ns = n >= 0 ? n : c;
       fb[i] = n >= 0 ? d.flags[ns] : (uint8_t)T_OBST;
       nv[i] = ST::ldw(A + di * P + ns);
-      phn[i] = (R)d.phi[ns];
+      phn[i] = (R)phi_work<R>(d)[ns];
     }
     int tn[Q];  // type of each incoming PDF's source
 #pragma unroll
@@ -1342,7 +1356,7 @@ __device__ __forceinline__ void stream_collide_if_body(const Dev& d, const Geom&
     }
     // Eq. nm-fslbm-mass-flux over i = 1..Q-1 (gas and walls carry none), in
     // the working precision (FP64 in the FP64 path)
-    const R phx = (R)d.phi[c];
+    const R phx = (R)phi_work<R>(d)[c];
     const int clsx = fl & (F_NF | F_NE);
     const bool thurey = !(p.options & 1u);
     R dm = (R)0;
@@ -1444,7 +1458,7 @@ __device__ __forceinline__ void fill_body(const Dev& d, const Geom& g) {
   // commit the fill levels computed by the stream-collide pass
   FSL_GRID_LOOP(k, nif) {
     const int c = lif[k];
-    d.phi[c] = d.phinew[c];
+    put_phi(d, c, d.phinew[c]);
   }
   // gas neighbours of filled cells become new interface cells; a neighbour
   // about to empty is kept (filling wins)
@@ -1460,7 +1474,7 @@ __device__ __forceinline__ void fill_body(const Dev& d, const Geom& g) {
         if ((d.flags[n] & F_TYPE) == T_GAS) {
           const uint8_t old = byte_or(d.flags, n, (uint8_t)(F_NEW | T_IF));
           if (!(old & F_NEW)) {
-            d.phi[n] = 0.0;
+            put_phi(d, n, 0.0);
             d.mass[n] = 0.0;
             created = true;
           }
@@ -1510,7 +1524,7 @@ __device__ __forceinline__ void empty_body(const Dev& d, const Geom& g) {
         density<Q, SH, R>(fin, rho, drho);
         d.rho[n] = (double)rho;
         d.mass[n] = (double)rho;
-        d.phi[n] = 1.0;
+        put_phi(d, n, 1.0);
         won = true;
       }
     }
@@ -1569,12 +1583,12 @@ __device__ __forceinline__ void finalise_share_body(const Dev& d, const Geom& g)
       if (fill) {
         mex = (d.phi[c] - 1.0) * d.rho[c];
         d.flags[c] = (uint8_t)((fl & ~F_TYPE) | T_LIQ);
-        d.phi[c] = 1.0;
+        put_phi(d, c, 1.0);
         d.mass[c] = d.rho[c];
       } else {
         mex = d.phi[c] * d.rho[c];
         d.flags[c] = (uint8_t)((fl & ~F_TYPE) | T_GAS);
-        d.phi[c] = 0.0;
+        put_phi(d, c, 0.0);
         d.mass[c] = 0.0;
         atomicAdd(&ctrl->n_emptied, 1u);
       }
@@ -1601,8 +1615,8 @@ __global__ void __launch_bounds__(256) kb_finalise_share(MemberTable t) {
 // block touches a wall or obstacle uses a two-point difference over the
 // non-obstacle cells instead (narrowed stencil near obstacles).  RC is the
 // compute type: FP64 in the FP64 path, FP32 otherwise.
-template <class RC>
-__device__ inline void normal_py(const Geom& g, const uint8_t* flags, const double* phi, int x,
+template <class RC, class PT>
+__device__ inline void normal_py(const Geom& g, const uint8_t* flags, const PT* phi, int x,
                                  int y, int z, RC* n) {
   const int p[3] = {x, y, z};
   const int c = x + g.sx * (y + g.ny * z);
@@ -1643,8 +1657,8 @@ __device__ inline void normal_py(const Geom& g, const uint8_t* flags, const doub
   }
 }
 
-template <class RC>
-__device__ inline void unit_normal(const Geom& g, const uint8_t* flags, const double* phi, int x,
+template <class RC, class PT>
+__device__ inline void unit_normal(const Geom& g, const uint8_t* flags, const PT* phi, int x,
                                    int y, int z, RC* nh) {
   RC n[3];
   normal_py<RC>(g, flags, phi, x, y, z, n);
@@ -1667,8 +1681,8 @@ __device__ __forceinline__ int wrapc(int v, int n) {
 
 // K = -div(n_hat), central differences over the face neighbours; a wall side
 // is replaced by the centre value.
-template <class RC>
-__device__ inline RC curvature(const Geom& g, const uint8_t* flags, const double* phi, int x,
+template <class RC, class PT>
+__device__ inline RC curvature(const Geom& g, const uint8_t* flags, const PT* phi, int x,
                                int y, int z) {
   RC nc[3];
   unit_normal<RC>(g, flags, phi, x, y, z, nc);
@@ -1703,8 +1717,8 @@ __device__ inline RC curvature(const Geom& g, const uint8_t* flags, const double
 // The same curvature for a cell whose distance-2 neighbourhood holds no wall
 // or obstacle: no type checks, wrapped coordinates computed once.  Same
 // operation order as curvature(), so the results are identical.
-template <class RC>
-__device__ inline RC curvature_open(const Geom& g, const double* phi, int x, int y, int z) {
+template <class RC, class PT>
+__device__ inline RC curvature_open(const Geom& g, const PT* phi, int x, int y, int z) {
   int X[5], Y[5], Z[5];
 #pragma unroll
   for (int o = 0; o < 5; ++o) {
@@ -1774,8 +1788,8 @@ __device__ __forceinline__ bool open_neighbourhood(const Geom& g, int x, int y, 
   return true;
 }
 
-template <class RC>
-__device__ inline RC curvature_any(const Geom& g, const uint8_t* flags, const double* phi, int x,
+template <class RC, class PT>
+__device__ inline RC curvature_any(const Geom& g, const uint8_t* flags, const PT* phi, int x,
                                    int y, int z) {
   return open_neighbourhood(g, x, y, z) ? curvature_open<RC>(g, phi, x, y, z)
                                         : curvature<RC>(g, flags, phi, x, y, z);
@@ -1894,7 +1908,7 @@ __device__ __forceinline__ void refill_body(const Dev& d, const Geom& g, const P
     int dn = -1;
     if (scheme == 1 || scheme == 3) {
       R n3[3];
-      normal_py<R>(g, d.flags, d.phi, x, y, z, n3);
+      normal_py<R>(g, d.flags, phi_work<R>(d), x, y, z, n3);
       R best = (R)0;
       for (int j = 1; j < Q; ++j) {
         if (!((vmask >> j) & 1u)) continue;
@@ -2026,7 +2040,7 @@ __device__ __forceinline__ void excess_gather_body(const Dev& d, const Geom& g) 
     for (int i = 1; i < Q; ++i)
       if (fb[i] & (F_TO_LIQ | F_TO_GAS)) sum += d.mex[ns[i]];
     d.mass[r] = d.mass[r] + sum;
-    d.phi[r] = d.mass[r] / d.rho[r];
+    put_phi(d, r, d.mass[r] / d.rho[r]);
   }
 }
 template <int Q>
@@ -2135,7 +2149,7 @@ __device__ __forceinline__ void classify_body(const Dev& d, const Geom& g, const
         int x, y, z;
         cell_xyz(g, c, x, y, z);
         nf |= iface_class<Q>(g, d.flags, x, y, z);
-        d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, d.phi, x, y, z) : 0.0;
+        d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, phi_work<R>(d), x, y, z) : 0.0;
       }
       d.flags[c] = nf;
     }
@@ -2152,6 +2166,13 @@ __global__ void __launch_bounds__(128, 4) kb_classify(MemberTable t) {
   classify_body<Q, ST>(d, g, p);
 }
 
+
+// The FP32 copy of every fill level (state loaded from a checkpoint).
+static __global__ void k_phif_from_phi(Dev d, Geom g) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < g.cells;
+       c += (long long)gridDim.x * blockDim.x)
+    d.phif[c] = (float)d.phi[c];
+}
 
 // The interface list of the current step from the flags (initial state, state
 // loaded from a checkpoint).
@@ -2319,7 +2340,7 @@ static __global__ void k_init_types(Dev d, Geom g, const double* phi0, const uin
       else { t = T_IF; ph = v; }
     }
     d.flags[c] = t;
-    d.phi[c] = ph;
+    put_phi(d, c, ph);
   }
 }
 
@@ -2395,7 +2416,7 @@ __global__ void k_init_classes(Dev d, Geom g, Phys p) {
     const uint8_t fl = d.flags[c];
     if ((fl & F_TYPE) != T_IF) continue;
     d.flags[c] = (uint8_t)((fl & ~(F_NF | F_NE)) | iface_class<Q>(g, d.flags, x, y, z));
-    d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, d.phi, x, y, z) : 0.0;
+    d.kappa[c] = (p.sigma != 0.0) ? (double)curvature_any<R>(g, d.flags, phi_work<R>(d), x, y, z) : 0.0;
   }
 }
 
