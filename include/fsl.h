@@ -255,6 +255,16 @@ int fsl_get_variant(const fsl_handle* h);
 enum { FSL_KERNEL_STREAM_COLLIDE = 1, FSL_KERNEL_BULK_PASS = 2 };
 fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4);
 
+/* Self-check of the library's bounded device waits (failure path).  Launches
+ * one block on the bound stream that waits at the conversion phase's grid
+ * barrier for an arrival that never comes; the wait gives up after its time
+ * bound (0.2 s), the handle's timeout bit is latched, and from then on
+ * fsl_observe(FSL_OBS_STATUS) reports FSL_ERR_TIMEOUT, as after any device
+ * wait that gave up.  Nothing else of the state changes; the CUDA context
+ * stays usable.  Synchronises the stream.  FSL_ERR_STATE before
+ * fsl_init_fill. */
+fsl_status fsl_selftest_wait(fsl_handle* h);
+
 /* Total mass of a state held in caller-owned device arrays, for callers that
  * cannot allocate device memory when they need it (inside a host callback or
  * another allocator, under a fixed device-memory budget, or in a loop that

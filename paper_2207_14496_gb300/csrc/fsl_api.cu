@@ -1251,6 +1251,15 @@ fsl_status fsl_kernel_stats(fsl_handle* h, int kernel, int reps, double* out4) {
   return FSL_OK;
 }
 
+fsl_status fsl_selftest_wait(fsl_handle* h) {
+  if (!h) return FSL_ERR_ARG;
+  if (!h->ready) return FSL_ERR_STATE;
+  k_barrier_selftest<<<1, 256, 0, h->stream>>>(h->d);
+  FSL_CK(cudaGetLastError());
+  FSL_CK(cudaStreamSynchronize(h->stream));
+  return FSL_OK;
+}
+
 const char* fsl_status_string(fsl_status s) {
   switch (s) {
     case FSL_OK: return "ok";

@@ -35,7 +35,8 @@ struct Ctrl {
   int trace_every;     // 0: no trace
   int trace_count;     // records written (ring index = count % capacity)
   unsigned timeout;    // error bits: 1 CAS retry cap, 2 refill without source, 4 copy wait gave up,
-                       // 8 bubble union retry cap, 16 grid barrier wait gave up
+                       // 8 bubble union retry cap, 16 grid barrier wait gave up,
+                       // 32 a self-checked barrier passed that could not
   unsigned n_emptied;  // to-gas cells actually converted this step
   unsigned end_blocks; // end-of-step blocks finished
   unsigned n_tiles;    // tiles holding liquid cells, listed this step (16/32-bit path)

@@ -2087,6 +2087,21 @@ __device__ __forceinline__ bool grid_barrier(Ctrl* ctrl, unsigned target) {
   __syncthreads();
   return ok != 0;
 }
+// Self-check of the bounded wait: one block arrives at a grid barrier whose
+// target needs one more arrival than can come, gives up after the time
+// bound, latches timeout bit 16, and puts the arrival count back.
+static __global__ void k_barrier_selftest(Dev d) {
+  Ctrl* ctrl = d.ctrl;
+  __shared__ unsigned before;
+  if (threadIdx.x == 0) before = *(volatile unsigned*)&ctrl->bar;
+  __syncthreads();
+  const bool ok = grid_barrier(ctrl, before + 2u);
+  if (threadIdx.x == 0) {
+    ctrl->bar = before;
+    if (ok) atomicOr(&ctrl->timeout, 32u);  // not expected: no second arrival exists
+  }
+}
+
 template <int Q, class ST>
 __global__ void __launch_bounds__(256) k_convert(Dev d, Geom g, Phys p) {
   Ctrl* ctrl = d.ctrl;

@@ -104,6 +104,8 @@ _lib.fsl_adjoint_backward.argtypes = [_VP, _VP, _VP]
 _lib.fsl_adjoint_backward.restype = ctypes.c_int
 _lib.fsl_adjoint_destroy.argtypes = [_VP]
 _lib.fsl_adjoint_destroy.restype = ctypes.c_int
+_lib.fsl_selftest_wait.argtypes = [_VP]
+_lib.fsl_selftest_wait.restype = ctypes.c_int
 _lib.fsl_status_string.argtypes = [ctypes.c_int]
 _lib.fsl_status_string.restype = ctypes.c_char_p
 _lib.fsl_last_error.restype = ctypes.c_char_p
@@ -118,7 +120,7 @@ EXPORTED = ("fsl_workspace_bytes", "fsl_create", "fsl_init_fill", "fsl_step", "f
             "fsl_status_string", "fsl_last_error", "fsl_total_mass_noalloc", "fsl_set_variant",
             "fsl_get_variant", "fsl_batch_create", "fsl_batch_step", "fsl_batch_destroy",
             "fsl_adjoint_workspace_bytes", "fsl_adjoint_create", "fsl_adjoint_forward",
-            "fsl_adjoint_backward", "fsl_adjoint_destroy")
+            "fsl_adjoint_backward", "fsl_adjoint_destroy", "fsl_selftest_wait")
 VARIANTS = {"default": 0, "pair": 1, "pair_r128": 2, "pair_r96": 3, "tma": 4, "quad64": 5,
             "warp_tma": 6, "pair_pipe": 7, "pair_r80": 8, "cpa": 9, "cpa_deep": 10,
             "cpa_r96": 11, "seg": 12, "seg_r128": 13,
@@ -300,6 +302,11 @@ class Sim:
     def status(self):
         v = self._obs(OBS_STATUS, np.zeros(2, dtype=np.int64))
         return int(v[0]), int(v[1])
+
+    def selftest_wait(self):
+        """Make one bounded device wait give up (fsl_selftest_wait): the
+        handle then reports the timeout status."""
+        _check(_lib.fsl_selftest_wait(self.h), "fsl_selftest_wait")
 
     @property
     def step_count(self) -> int:
