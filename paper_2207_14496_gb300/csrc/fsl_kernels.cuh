@@ -147,6 +147,15 @@ __device__ __forceinline__ void feq_all(R* out, R rho, R drho, R ux, R uy, R uz,
     feq_all<Q, SHIFT, R, I + 1>(out, rho, drho, ux, uy, uz, usq);
   }
 }
+// The same equilibrium for a direction given as an (unrolled-loop) value:
+// identical operations, so identical results.
+template <int Q, bool SHIFT, class R>
+__device__ __forceinline__ R feq_c(int i, R rho, R drho, R ux, R uy, R uz, R usq) {
+  const R w = (R)wgt<Q>(i);
+  R cu = dot3r<R>(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2), ux, uy, uz);
+  if (!SHIFT) return w * rho * ((R)1 + (R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * usq);
+  return w * (drho + rho * ((R)3 * cu + (R)4.5 * cu * cu - (R)1.5 * usq));
+}
 template <int Q, class R, int I = 0>
 __device__ __forceinline__ void guo_all(R* out, R ux, R uy, R uz, R Fx, R Fy, R Fz) {
   if constexpr (I < Q) {
@@ -1328,32 +1337,6 @@ __device__ __forceinline__ void stream_collide_if_body(const Dev& d, const Geom&
                                        : pv + p.sigma * d.kappa[c];
     const R rg = (R)(3.0 * pg);  // rho_G = p_G / c_s^2
     const R drg = (R)(3.0 * pg - 1.0);
-    R feg[Q];
-    feq_all<Q, SH, R>(feg, rg, drg, utx, uty, utz, utsq);
-    // Source cell of each incoming PDF (-1 beyond a no-slip wall), then its
-    // flag byte, stored value and fill level: every load has a valid address
-    // whatever the type turns out to be, so they are all in flight at once
-    // and the type only selects among the values.
-    uint8_t fb[Q];
-    R nv[Q], phn[Q];
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      int di;
-      const int n = nb.geo_source<Q>(i, di);
-      const int ns = n >= 0 ? n : c;
-      fb[i] = n >= 0 ? d.flags[ns] : (uint8_t)T_OBST;
-      nv[i] = ST::ldw(A + di * P + ns);
-      phn[i] = (R)phi_work<R>(d)[ns];
-    }
-    int tn[Q];  // type of each incoming PDF's source
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int t = fb[i] & F_TYPE;
-      tn[i] = t;
-      if (is_fluid(t)) fin[i] = nv[i];                         /* neighbour or mirror image */
-      else if (t == T_OBST) fin[i] = own[opp(i)];             /* halfway bounce-back */
-      else fin[i] = feg[i] + feg[opp(i)] - own[opp(i)];       /* anti-bounce-back from gas */
-    }
     // Eq. nm-fslbm-mass-flux over i = 1..Q-1 (gas and walls carry none), in
     // the working precision (FP64 in the FP64 path)
     const R phx = (R)phi_work<R>(d)[c];
@@ -1361,31 +1344,67 @@ __device__ __forceinline__ void stream_collide_if_body(const Dev& d, const Geom&
     const bool thurey = !(p.options & 1u);
     R dm = (R)0;
     bool dm_has = false;
+    // Directions in opposite pairs (0 alone, then (1, 2), (3, 4), ...): per
+    // direction the source cell of the incoming PDF (-1 beyond a no-slip
+    // wall), its flag byte, stored value and fill level (every load with a
+    // valid address whatever the type turns out to be, the type only selects
+    // among the values), then the pair's two flux terms, which need exactly
+    // the pair's values: the sum still runs over i = 1, 2, 3, ... in order,
+    // and a pair's loads are dead once its terms are added.
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const int io = opp(i);
-      // the cell exchanging PDFs with x along c_i (x + c_i, or its mirror
-      // image across a free-slip wall) is the source of the incoming f_io
-      const int t = tn[io];
-      if (t != T_LIQ && t != T_IF) continue;
-      // f_in = fin[io] (what arrives from it), f_out = f*_i(x) = own[i]
-      R dd;
-      const R both = fin[io] - own[i];
-      if (t == T_LIQ) {
-        dd = both;
-      } else {
-        const int clsn = fb[io] & (F_NF | F_NE);
-        const R f_in = SH ? fin[io] + (R)wgt<Q>(io) : fin[io];
-        const R f_out = SH ? own[i] + (R)wgt<Q>(i) : own[i];
-        R br;
-        if (!thurey) br = both;
-        else if (clsx == 0) br = (clsn == F_NF) ? f_in : (clsn == F_NE) ? -f_out : both;
-        else if (clsx == F_NF) br = (clsn == F_NF) ? both : -f_out;
-        else br = (clsn == F_NE) ? both : f_in;
-        dd = (R)0.5 * (phx + phn[io]) * br;
+    for (int k = 0; k <= (Q - 1) / 2; ++k) {
+      const int i0 = k == 0 ? 0 : 2 * k - 1;
+      const int np = k == 0 ? 1 : 2;
+      // gas equilibria of the pair (Eq. nm-fslbm-boundary-condition)
+      const R fe0 = feq_c<Q, SH, R>(i0, rg, drg, utx, uty, utz, utsq);
+      const R fe1 = np == 2 ? feq_c<Q, SH, R>(i0 + 1, rg, drg, utx, uty, utz, utsq) : fe0;
+      uint8_t fb2[2];
+      R ph2[2];
+      int tn2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (h >= np) break;
+        const int i = i0 + h;
+        int di;
+        const int n = nb.geo_source<Q>(i, di);
+        const int ns = n >= 0 ? n : c;
+        fb2[h] = n >= 0 ? d.flags[ns] : (uint8_t)T_OBST;
+        const R nv = ST::ldw(A + di * P + ns);
+        ph2[h] = (R)phi_work<R>(d)[ns];
+        const int t = fb2[h] & F_TYPE;
+        tn2[h] = t;
+        const R fa = h == 0 ? fe0 : fe1, fo = h == 0 ? fe1 : fe0;
+        if (is_fluid(t)) fin[i] = nv;                         /* neighbour or mirror image */
+        else if (t == T_OBST) fin[i] = own[opp(i)];          /* halfway bounce-back */
+        else fin[i] = fa + fo - own[opp(i)];                 /* anti-bounce-back from gas */
       }
-      dm = dm_has ? dm + dd : dd;
-      dm_has = true;
+      if (np < 2) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = i0 + h, io = opp(i), ho = 1 - h;  // io = i0 + ho
+        // the cell exchanging PDFs with x along c_i (x + c_i, or its mirror
+        // image across a free-slip wall) is the source of the incoming f_io
+        const int t = tn2[ho];
+        if (t != T_LIQ && t != T_IF) continue;
+        // f_in = fin[io] (what arrives from it), f_out = f*_i(x) = own[i]
+        R dd;
+        const R both = fin[io] - own[i];
+        if (t == T_LIQ) {
+          dd = both;
+        } else {
+          const int clsn = fb2[ho] & (F_NF | F_NE);
+          const R f_in = SH ? fin[io] + (R)wgt<Q>(io) : fin[io];
+          const R f_out = SH ? own[i] + (R)wgt<Q>(i) : own[i];
+          R br;
+          if (!thurey) br = both;
+          else if (clsx == 0) br = (clsn == F_NF) ? f_in : (clsn == F_NE) ? -f_out : both;
+          else if (clsx == F_NF) br = (clsn == F_NF) ? both : -f_out;
+          else br = (clsn == F_NE) ? both : f_in;
+          dd = (R)0.5 * (phx + ph2[ho]) * br;
+        }
+        dm = dm_has ? dm + dd : dd;
+        dm_has = true;
+      }
     }
     const double m_new = dm_has ? d.mass[c] + (double)dm : d.mass[c];
     R fout[Q], rho;
