@@ -1490,7 +1490,10 @@ __device__ __forceinline__ void fill_body(const Dev& d, const Geom& g) {
     if (lane >= 1 && lane < Q) {
       n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
       if (n >= 0) {
-        if ((d.flags[n] & F_TYPE) == T_GAS) {
+        // one load of the flag byte: marks are only set by the interface
+        // pass, and clearing one twice is harmless
+        const uint8_t fn = d.flags[n];
+        if ((fn & F_TYPE) == T_GAS) {
           const uint8_t old = byte_or(d.flags, n, (uint8_t)(F_NEW | T_IF));
           if (!(old & F_NEW)) {
             put_phi(d, n, 0.0);
@@ -1498,7 +1501,7 @@ __device__ __forceinline__ void fill_body(const Dev& d, const Geom& g) {
             created = true;
           }
         }
-        if (d.flags[n] & F_TO_GAS) byte_and(d.flags, n, F_TO_GAS);
+        if (fn & F_TO_GAS) byte_and(d.flags, n, F_TO_GAS);
       }
     }
     warp_append(created, n, &ctrl->n_new, d.l_new);
@@ -1902,7 +1905,9 @@ __device__ __forceinline__ void refill_body(const Dev& d, const Geom& g, const P
     if (lane >= 1 && lane < Q) {
       n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
       valid = valid_src(d.flags, n);
-      if (valid) stored_moments_w<Q, ST>(B, P, n, p, nr, ndr, nu);
+      // loaded whatever the flag says (the cell itself beyond a wall), so that
+      // the loads need not wait for it; only valid neighbours are used below
+      stored_moments_w<Q, ST>(B, P, n >= 0 ? n : c, p, nr, ndr, nu);
     }
     const unsigned vmask = __ballot_sync(FULL, valid);
     const int count = __popc(vmask);
@@ -2047,19 +2052,26 @@ __device__ __forceinline__ void excess_gather_body(const Dev& d, const Geom& g) 
     cell_xyz(g, r, x, y, z);
     Nbr nb;
     nb.setup(g, x, y, z);
-    int ns[Q];
+    const double m0 = d.mass[r], rr = d.rho[r];
+    // flag bytes and shares of all neighbours with valid addresses (the cell
+    // itself beyond a wall), so that all loads are in flight together and the
+    // marks only select which shares are summed
     uint8_t fb[Q];
+    double sv[Q];
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      ns[i] = nb.at(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2));
-      fb[i] = ns[i] >= 0 ? d.flags[ns[i]] : (uint8_t)0;
+      const int n = nb.at(dir_c(i, 0), dir_c(i, 1), dir_c(i, 2));
+      const int ns = n >= 0 ? n : r;
+      fb[i] = n >= 0 ? d.flags[ns] : (uint8_t)0;
+      sv[i] = d.mex[ns];
     }
     double sum = 0.0;
 #pragma unroll
     for (int i = 1; i < Q; ++i)
-      if (fb[i] & (F_TO_LIQ | F_TO_GAS)) sum += d.mex[ns[i]];
-    d.mass[r] = d.mass[r] + sum;
-    put_phi(d, r, d.mass[r] / d.rho[r]);
+      if (fb[i] & (F_TO_LIQ | F_TO_GAS)) sum += sv[i];
+    const double m = m0 + sum;
+    d.mass[r] = m;
+    put_phi(d, r, m / rr);
   }
 }
 template <int Q>
