@@ -2183,7 +2183,11 @@ __device__ __forceinline__ void classify_body(const Dev& d, const Geom& g, const
   int* lnext = list_if(d, ctrl->step + 1);
   // every interface cell of the next step was interface, new or liquid turned
   // interface in this one: the next step's list is built here
-  FSL_WARP_LOOP(k, ok, a + b + e) {
+  // block-uniform loop (the append below is block-wide; 128 threads)
+  const unsigned n = a + b + e;
+  for (unsigned base = blockIdx.x * 128u; base < n; base += gridDim.x * 128u) {
+    const unsigned k = base + threadIdx.x;
+    const bool ok = k < n;
     const int c = !ok ? 0 : (k < a ? lif[k] : (k < a + b ? d.l_new[k - a] : d.l_l2i[k - a - b]));
     bool is_if = false;
     if (ok) {
@@ -2199,7 +2203,7 @@ __device__ __forceinline__ void classify_body(const Dev& d, const Geom& g, const
       }
       d.flags[c] = nf;
     }
-    warp_append(is_if, c, &ctrl->n_if_next, lnext);
+    block_append<128>(is_if, c, &ctrl->n_if_next, lnext);
   }
 }
 template <int Q, class ST>

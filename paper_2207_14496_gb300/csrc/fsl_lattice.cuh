@@ -253,6 +253,33 @@ __device__ __forceinline__ void warp_append(bool pred, int value, unsigned* coun
   if (pred) list[base + __popc(mask & ((1u << lane) - 1u))] = value;
 }
 
+// The same for a whole block of NT threads (all of them call it): one atomic
+// per block instead of one per warp.  Lists with one entry for most threads
+// (the next step's interface list) otherwise queue thousands of same-address
+// atomics per step.
+template <int NT>
+__device__ __forceinline__ void block_append(bool pred, int value, unsigned* count, int* list) {
+  constexpr int NW = NT / 32;
+  __shared__ unsigned wbase[NW];
+  __shared__ unsigned bbase;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned mask = __ballot_sync(0xffffffffu, pred);
+  if (lane == 0) wbase[warp] = (unsigned)__popc(mask);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = 0;
+    for (int w = 0; w < NW; ++w) {
+      const unsigned c = wbase[w];
+      wbase[w] = t;
+      t += c;
+    }
+    bbase = t ? atomicAdd(count, t) : 0u;
+  }
+  __syncthreads();
+  if (pred) list[bbase + wbase[warp] + (unsigned)__popc(mask & ((1u << lane) - 1u))] = value;
+  __syncthreads();  // wbase and bbase are reused by the block's next call
+}
+
 // Atomic OR / AND on the byte of a flag array through its aligned 32-bit word.
 __device__ __forceinline__ uint8_t byte_or(uint8_t* a, int c, uint8_t bits) {
   unsigned* word = reinterpret_cast<unsigned*>(reinterpret_cast<uintptr_t>(a + c) & ~uintptr_t(3));
