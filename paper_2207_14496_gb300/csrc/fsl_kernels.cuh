@@ -1526,24 +1526,30 @@ __device__ __forceinline__ void empty_body(const Dev& d, const Geom& g) {
   const int lane = threadIdx.x & 31;
   FSL_WARP_PER_ITEM(k, ne) {
     const int c = d.l_empty[k];
-    if (!(d.flags[c] & F_TO_GAS)) continue;  // kept by a filling neighbour (warp-uniform)
     int x, y, z;
     cell_xyz(g, c, x, y, z);
+    // the neighbour's flag byte is loaded together with the cell's own
     int n = -1;
-    bool won = false;
+    uint8_t fn = 0;
     if (lane >= 1 && lane < Q) {
       n = nb_at(g, x, y, z, rc(lane, 0), rc(lane, 1), rc(lane, 2));
-      if (n >= 0 && (d.flags[n] & F_TYPE) == T_LIQ &&
-          byte_retype(d.flags, n, T_LIQ, T_IF, &ctrl->timeout)) {
-        // the liquid cell's density of this step, recomputed exactly as the
-        // stream-collide pass obtained it
-        int nx_, ny_, nz_;
-        cell_xyz(g, n, nx_, ny_, nz_);
-        Nbr nb;
-        nb.setup(g, nx_, ny_, nz_);
-        R fin[Q], rho, drho;
-        pull_liquid<Q, ST>(A, g.plane, d.flags, nb, n, (d.flags[n] & F_NEAR_OBST) != 0, fin);
-        density<Q, SH, R>(fin, rho, drho);
+      if (n >= 0) fn = d.flags[n];
+    }
+    if (!(d.flags[c] & F_TO_GAS)) continue;  // kept by a filling neighbour (warp-uniform)
+    bool won = false;
+    if (n >= 0 && (fn & F_TYPE) == T_LIQ) {
+      // the liquid cell's density of this step, recomputed exactly as the
+      // stream-collide pass obtained it (its PDFs are loaded before the type
+      // change is claimed, so that the two round trips overlap; a lane whose
+      // claim fails drops them)
+      int nx_, ny_, nz_;
+      cell_xyz(g, n, nx_, ny_, nz_);
+      Nbr nb;
+      nb.setup(g, nx_, ny_, nz_);
+      R fin[Q], rho, drho;
+      pull_liquid<Q, ST>(A, g.plane, d.flags, nb, n, (fn & F_NEAR_OBST) != 0, fin);
+      density<Q, SH, R>(fin, rho, drho);
+      if (byte_retype(d.flags, n, T_LIQ, T_IF, &ctrl->timeout)) {
         d.rho[n] = (double)rho;
         d.mass[n] = (double)rho;
         put_phi(d, n, 1.0);
