@@ -298,8 +298,8 @@ fsl_status fsl_total_mass_noalloc(const fsl_config* cfg, const void* d_pdf,
  * the bubble model, each kernel of a step is launched once for all members
  * of a lattice and storage (up to 256 members per launch, one member per
  * blockIdx.y; the member reads its pointers, geometry and parameters from a
- * record in its own workspace), so a step of the whole batch costs about a
- * dozen launches; otherwise each member's kernels form an independent branch
+ * record in its own workspace), so a step of the whole batch costs ten
+ * launches; otherwise each member's kernels form an independent branch
  * (a child graph per member, no edges between members).  Either way the GPU
  * runs the domains side by side instead of one after another.
  *   handles: host array of n >= 1 handles, all initialised (fsl_init_fill or
