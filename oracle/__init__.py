@@ -10,10 +10,12 @@ mass conservation, resting pool, standing-wave frequency and damping,
 Young-Laplace jump, TRT Poiseuille, hand-built refilling neighbourhoods,
 normal/curvature exactness, free-slip plug flow, Smagorinsky closure, one
 periodic layer = D2Q9, and the bubble model: library labelling, p V through
-compression, merge and split, pressures unchanged by a mirrored grid).  Parity unpinned
-(pinned only by oracle = GPU): the Thuerey flux table (R5), excess-mass
-receivers (R3), conflict priority (R6), neighbour means (R7), obstacle
-narrowing of normals (R11), geometry conventions and observables.
+compression, merge and split, pressures unchanged by a mirrored grid), and
+on hand-built states: the mass flux with every pair of Thuerey classes (R5),
+the excess-mass receivers and shares and the lost-mass accumulator (R3),
+the conflict priority (R6), the refilling means (R7), the obstacle-narrowed
+normals (R11), the trace observables (R14) and the wave's cell convention
+(R13).
 """
 from __future__ import annotations
 
