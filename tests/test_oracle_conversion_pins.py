@@ -204,7 +204,7 @@ def test_filling_wins_over_an_emptying_neighbour(q):
     """R6 (Sec. 2.2, separation prioritised): an interface cell whose fill
     level falls below -eps stays interface when a neighbour fills in the same
     step; without the filling neighbour it empties and its liquid neighbours
-    become interface."""
+    become interface (R18: with their density of the step as mass)."""
     for filling in (True, False):
         o, types, phi, f, mass, c = _flat_layer(q)
         a, b = (0, 3, 3), (0, 3, 4)
@@ -219,6 +219,17 @@ def test_filling_wins_over_an_emptying_neighbour(q):
             assert t[a] == oracle.IFACE and t[b] == oracle.GAS
             assert t[0, 2, 4] == oracle.IFACE          # liquid below b
             assert t[0, 2, 1] == oracle.LIQUID          # away from b
+            # R18: a liquid cell turned interface starts from m = its density
+            # of the step (the rest equilibrium's, sum w_i = 1), then receives
+            # its shares of b's (negative) excess m_b = -0.3 (R3)
+            shares = {}
+            for cv in c[1:]:
+                n = _neighbour(b, cv, types.shape, (True, False, True))
+                if n is not None and n != b and types[n] in (oracle.IFACE, oracle.LIQUID):
+                    shares[n] = shares.get(n, 0) + 1
+            nr = sum(shares.values())
+            want = 1.0 + shares[(0, 2, 4)] * (-0.3) / nr
+            assert abs(o.mass()[0, 2, 4] - want) < 1e-14
 
 
 # ------------------------------------------------------------------ refilling means
